@@ -1,0 +1,185 @@
+/*
+ * normgb.h -- C ABI of libnormgb, batched accurate normalization of vectors
+ * and quaternions on GB300 (sm_103a), following W. F. Mascarenhas, "Fast and
+ * accurate normalization of vectors and quaternions" (arXiv 1606.06508).
+ *
+ * For each vector x (length n) the library computes, with one correctly
+ * rounded IEEE operation per step and no fused multiply-add:
+ *   m = max |x_k|; the zero result when every x_k is zero;
+ *   x~ = c x with c = 1, sigma_min or sigma_max, the power of two that puts m
+ *        into [tau_min, tau_max]                    (Section 2, Eqs. (5)-(10),
+ *                                                    Table 2, Algs. 3 and 4);
+ *   r~ = sqrt(x~_1^2 + ... + x~_n^2), h = 1/r~;
+ *   y_k = h x~_k  (the normalized vector x/|x|) and r = c^{-1} r~  (its norm)
+ *                                                   (Algs. 5, 6, 7; Eqs. (1), (2)).
+ * n <= 4 follows the printed algorithms (left-to-right sums); n >= 5 sums in
+ * a fixed canonical order (1024 slots and a halving tree) with
+ * tau_max = 2^53 (binary32) or 2^501 (binary64) so that up to 2^20 squares
+ * cannot overflow.  Every kernel mapping (thread, warp or block per vector)
+ * returns the same bits, and they equal a sequential evaluation of the same
+ * steps.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller.  Vectors are
+ *     stored contiguously: a dense batch is [count][dim] row-major (AoS); a
+ *     ragged batch packs vector i at x[offsets[i] .. offsets[i+1]).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *     default stream).  Argument errors are detected on the host before any
+ *     work is queued.  Data-dependent errors (bad ragged offsets) never stop a
+ *     kernel: the vector is skipped and a status word in the plan is set,
+ *     read back by ngb_query_status().
+ *   - count == 0 is a no-op returning NGB_OK.  Output arrays may alias the
+ *     corresponding input arrays (y == x, grad == g) but must not partly
+ *     overlap them.  No exception crosses the ABI; ngb_last_error() gives a
+ *     message for the last failing call of the calling thread.
+ */
+#ifndef NORMGB_H
+#define NORMGB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ngb_stream_t; /* same type as cudaStream_t */
+typedef struct ngb_plan ngb_plan;
+
+typedef enum ngb_status {
+  NGB_OK = 0,
+  NGB_ERR_INVALID_ARG = 1, /* null pointer, negative size, bad flag combination */
+  NGB_ERR_UNSUPPORTED = 2, /* dim or length beyond NGB_MAX_LEN, unsupported dtype */
+  NGB_ERR_BAD_OFFSETS = 3, /* ngb_query_status: some ragged vector had bad offsets */
+  NGB_ERR_CUDA = 4,        /* a CUDA runtime call failed (see ngb_last_error) */
+  NGB_ERR_NO_PLAN = 5      /* a ragged call without a plan, or a plan of another size/dtype */
+} ngb_status;
+
+/* flags of the normalize calls */
+#define NGB_VECTOR_SEMANTICS 0x1u /* dim == 4: zero input gives y = 0, not the quaternion (0,0,1,0) */
+#define NGB_VALIDATE_OFFSETS 0x2u /* ragged: also require offsets[0] == 0 */
+
+/* saved_code values (the factor c applied to x) */
+#define NGB_CODE_ONE 0       /* c = 1 */
+#define NGB_CODE_SIGMA_MIN 1 /* c = sigma_min: 2^100 (binary32), 2^592 (binary64) */
+#define NGB_CODE_SIGMA_MAX 2 /* c = sigma_max: 2^-66 / 2^-514 for n <= 4, 2^-75 / 2^-523 for n >= 5 */
+#define NGB_CODE_ZERO 3      /* zero input: zero result, no factor */
+
+#define NGB_MAX_LEN (1 << 20) /* longest vector */
+
+/*
+ * normalize_f32 / normalize_f64 -- forward normalization
+ * (Eqs. (1)-(2); Algorithms 3-7 of Sections 2-4).
+ *
+ *   x          input, count vectors (dense: count*dim values; ragged: offsets[count] values)
+ *   y          output x/|x|, same layout as x; may equal x; may be NULL to compute norms only
+ *   norm       nullable, [count]: r = c^{-1} r~ (+0 for a zero or zero-length vector)
+ *   saved_h    nullable, [count]: h = 1/r~ (needed by the backward pass)
+ *   saved_code nullable, [count] int8: NGB_CODE_* (needed by the backward pass)
+ *   count      number of vectors, 0 <= count < 2^31
+ *   dim        > 0: dense batch of vectors of this length (1 .. NGB_MAX_LEN);
+ *              0:   ragged batch described by offsets
+ *   offsets    ragged only: device int64[count+1], nondecreasing; NULL for dense
+ *   plan       ragged only: from ngb_plan_create (count and dtype must match); NULL for dense
+ *   flags      NGB_VECTOR_SEMANTICS, NGB_VALIDATE_OFFSETS
+ * Dense dim == 4 uses the quaternion zero result (0, 0, 1, 0) of Algorithm 7
+ * unless NGB_VECTOR_SEMANTICS is set; ragged vectors always use the vector
+ * rule.  A NaN component makes every output of its vector NaN.
+ * Returns NGB_OK once the work is queued.
+ */
+ngb_status normalize_f32(const float* x, float* y, float* norm, float* saved_h, int8_t* saved_code, int64_t count,
+                         int32_t dim, const int64_t* offsets, ngb_plan* plan, uint32_t flags, ngb_stream_t stream);
+ngb_status normalize_f64(const double* x, double* y, double* norm, double* saved_h, int8_t* saved_code,
+                         int64_t count, int32_t dim, const int64_t* offsets, ngb_plan* plan, uint32_t flags,
+                         ngb_stream_t stream);
+
+/*
+ * normalize_backward_f32 / _f64 -- vector-Jacobian product of y = x/|x|
+ * (the derivative of Eq. (1); the paper has no backward pass):
+ *   grad = (g - y (y . g)) / |x|, evaluated as dot = y . g (left to right for
+ *   n <= 4, the canonical order for n >= 5), grad_k = ((g_k - y_k dot) h) c,
+ * from the forward's y, saved_h and saved_code, so x is not read again.
+ * grad = +0 for a zero input vector.  grad may equal g.  Same layout, count,
+ * dim, offsets and plan rules as the forward call.
+ */
+ngb_status normalize_backward_f32(const float* y, const float* g, const float* saved_h, const int8_t* saved_code,
+                                  float* grad, int64_t count, int32_t dim, const int64_t* offsets, ngb_plan* plan,
+                                  uint32_t flags, ngb_stream_t stream);
+ngb_status normalize_backward_f64(const double* y, const double* g, const double* saved_h,
+                                  const int8_t* saved_code, double* grad, int64_t count, int32_t dim,
+                                  const int64_t* offsets, ngb_plan* plan, uint32_t flags, ngb_stream_t stream);
+
+/*
+ * Ragged plans.  A plan holds the device work lists (12 bytes per vector plus
+ * a few counters) for ragged batches of exactly `count` vectors of one dtype
+ * (dtype_bytes 4 or 8), the thread/warp/block mapping, and the CUDA graphs
+ * that replay the two launches of a call.  It is bound to count and dtype,
+ * not to the contents of the offsets, which may change between calls.
+ *   capacity    number of elements in the caller's x / y / g buffers, or 0 if
+ *               unknown; when > 0, a vector reaching past it is skipped and
+ *               reported as bad offsets instead of being read.
+ * ngb_plan_create allocates device memory (cudaMalloc) on the current device
+ * and synchronizes nothing; ngb_plan_destroy frees it (synchronizing the device).
+ * A plan must not be used by two streams at once.
+ */
+ngb_status ngb_plan_create(ngb_plan** out, int64_t count, int32_t dtype_bytes, int64_t capacity);
+ngb_status ngb_plan_destroy(ngb_plan* plan);
+
+/* The mapping: vectors with n <= thread_max (4..16) go one per thread, those
+ * with n <= warp_max (thread_max..1024) one per warp, longer ones one per block
+ * of block_threads (256 or 512) threads; grid_blocks persistent blocks
+ * (0: one full wave).  Results do not depend on it. */
+ngb_status ngb_plan_set_mapping(ngb_plan* plan, int32_t thread_max, int32_t warp_max, int32_t block_threads,
+                                int32_t grid_blocks);
+ngb_status ngb_plan_get_mapping(const ngb_plan* plan, int32_t* thread_max, int32_t* warp_max,
+                                int32_t* block_threads, int32_t* grid_blocks);
+
+/* Autotuner: times the candidate mappings on these offsets (device
+ * int64[count+1]) with CUDA events, using a scratch buffer of offsets[count]
+ * elements it allocates and frees, and keeps the fastest.  With a non-NULL
+ * cache_path the choice is read from / appended to that text file, keyed by
+ * GPU name, dtype, count, element total and a length histogram.
+ * Synchronizes the stream. */
+ngb_status ngb_plan_autotune(ngb_plan* plan, const int64_t* offsets, const char* cache_path, ngb_stream_t stream);
+
+/* Use (1) or stop using (0) CUDA-graph replay for this plan's calls.
+ * On by default.  Calls on a stream that is itself being captured launch
+ * directly. */
+ngb_status ngb_plan_set_graphs(ngb_plan* plan, int32_t enable);
+
+/* Synchronizes `stream`, then reports and clears the plan's status word:
+ * NGB_ERR_BAD_OFFSETS if a call since the last query skipped a vector with
+ * negative length, length > NGB_MAX_LEN, an end beyond `capacity`, or (with
+ * NGB_VALIDATE_OFFSETS) offsets[0] != 0. */
+ngb_status ngb_query_status(ngb_plan* plan, ngb_stream_t stream);
+
+/*
+ * normalize_to_rotation_f32 / _f64 -- Section 4: normalize quaternions
+ * q = (q1, q2, q3, q4) (scalar part q4) with Algorithm 7 and write the
+ * rotation matrix of the unit quaternion, row-major, 9 values per quaternion:
+ *   [1-2(q2^2+q3^2)  2(q1q2-q3q4)    2(q1q3+q2q4)  ]
+ *   [2(q1q2+q3q4)    1-2(q1^2+q3^2)  2(q2q3-q1q4)  ]
+ *   [2(q1q3-q2q4)    2(q2q3+q1q4)    1-2(q1^2+q2^2)]
+ * (the two diagonal entries printed with 2 q3^2 and 2 q2^2 are read as the
+ * unit-norm form of the general matrix).  q: [count][4]; R: [count][9];
+ * norm nullable [count].  The zero quaternion gives q^ = (0,0,1,0).
+ */
+ngb_status normalize_to_rotation_f32(const float* q, float* R, float* norm, int64_t count, ngb_stream_t stream);
+ngb_status normalize_to_rotation_f64(const double* q, double* R, double* norm, int64_t count, ngb_stream_t stream);
+
+/* Measurement aids (not the method): a streaming device copy of `bytes`
+ * bytes, the bandwidth ceiling for the same traffic; and the naive
+ * normalization y = x / sqrt(sum x_k^2) without scaling (it overflows and
+ * underflows), the baseline of Table 4, for dim 2..4. */
+ngb_status ngb_copy(void* dst, const void* src, int64_t bytes, ngb_stream_t stream);
+ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream);
+ngb_status naive_normalize_f64(const double* x, double* y, int64_t count, int32_t dim, ngb_stream_t stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* ngb_last_error(void);
+/* Library version string. */
+const char* ngb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NORMGB_H */

@@ -61,6 +61,9 @@ def _load():
                 b = getattr(lib, f"oracle_backward_{sfx}")
                 b.restype = ctypes.c_int
                 b.argtypes = [P, P, P, P, ctypes.c_int64, ctypes.c_int32, P, P]
+                rot = getattr(lib, f"oracle_rotation_{sfx}")
+                rot.restype = ctypes.c_int
+                rot.argtypes = [P, ctypes.c_int64, P, P]
             lib.oracle_ieee_check.restype = ctypes.c_int
             lib.oracle_ieee_check.argtypes = []
             _lib = lib
@@ -173,3 +176,17 @@ def normalize_threads(x, dim: int, offsets=None, flags: int = 0, threads: int = 
     if errors:
         raise ValueError(f"oracle failed: {errors}")
     return y, norm, h, code
+
+
+def rotation(q):
+    """Section 4: rotation matrices [count, 3, 3] of quaternions [count, 4]
+    (scalar part last) normalized by Algorithm 7, and their norms."""
+    q = np.ascontiguousarray(q)
+    sfx = _sfx(q.dtype)
+    count = q.size // 4
+    R = np.empty((count, 3, 3), dtype=q.dtype)
+    norm = np.empty(count, dtype=q.dtype)
+    rc = getattr(_load(), f"oracle_rotation_{sfx}")(_ptr(q), count, _ptr(R), _ptr(norm))
+    if rc != 0:
+        raise ValueError(f"oracle_rotation_{sfx} failed with code {rc}")
+    return R, norm

@@ -352,3 +352,37 @@ int SFX(oracle_backward)(const REAL *y, const REAL *g, const REAL *saved_h,
     free(work);
     return 0;
 }
+
+/* ---------------------------------------------------------------------- */
+/* Section 4: the rotation matrix of a quaternion (q1, q2, q3, q4) with scalar
+ * part q4, from its normalization q^ by Algorithm 7 and the unit-norm form of
+ * the matrix.  The printed unit-norm matrix has "2 q3^2" in its first and
+ * "2 q2^2" in its last diagonal entry; the general matrix at |q| = 1 gives
+ * 1 - 2(q2^2 + q3^2) and 1 - 2(q1^2 + q2^2), used here.  Each entry is
+ * evaluated as written, row-major into R[9]. */
+static void SFX(rotation_one)(const REAL *q, REAL *R, REAL *r)
+{
+    REAL u[4], h;
+    SFX(normalize4)(q, u, r, &h, 1);
+    REAL q1 = u[0], q2 = u[1], q3 = u[2], q4 = u[3];
+    R[0] = 1 - 2 * (q2 * q2 + q3 * q3);
+    R[1] = 2 * (q1 * q2 - q3 * q4);
+    R[2] = 2 * (q1 * q3 + q2 * q4);
+    R[3] = 2 * (q1 * q2 + q3 * q4);
+    R[4] = 1 - 2 * (q1 * q1 + q3 * q3);
+    R[5] = 2 * (q2 * q3 - q1 * q4);
+    R[6] = 2 * (q1 * q3 - q2 * q4);
+    R[7] = 2 * (q2 * q3 + q1 * q4);
+    R[8] = 1 - 2 * (q1 * q1 + q2 * q2);
+}
+
+int SFX(oracle_rotation)(const REAL *q, int64_t count, REAL *R, REAL *norm)
+{
+    if (count < 0) return 1;
+    for (int64_t i = 0; i < count; ++i) {
+        REAL r;
+        SFX(rotation_one)(q + 4 * i, R + 9 * i, &r);
+        if (norm) norm[i] = r;
+    }
+    return 0;
+}

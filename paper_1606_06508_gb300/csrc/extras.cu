@@ -1,0 +1,180 @@
+// extras.cu -- device properties, the quaternion-to-rotation-matrix kernel and
+// two measurement aids (a plain copy and the unscaled "naive" normalization).
+#include <mutex>
+
+#include "ngb_internal.h"
+#include "ngb_rowpath.cuh"
+
+namespace ngb {
+
+int device_sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
+// ---------------------------------------------------------------------------
+// Section 4: a quaternion q = (q1, q2, q3, q4) with scalar part q4 is
+// normalized by Algorithm 7 and turned into the rotation matrix of the unit
+// quaternion.  The printed unit-norm matrix has two typos (2 q3^2 and 2 q2^2
+// inside the first and last diagonal entries); the entries used here are the
+// ones the general formula gives for |q| = 1:
+//   R00 = 1 - 2 (q2^2 + q3^2)    R01 = 2 (q1 q2 - q3 q4)    R02 = 2 (q1 q3 + q2 q4)
+//   R10 = 2 (q1 q2 + q3 q4)      R11 = 1 - 2 (q1^2 + q3^2)  R12 = 2 (q2 q3 - q1 q4)
+//   R20 = 2 (q1 q3 - q2 q4)      R21 = 2 (q2 q3 + q1 q4)    R22 = 1 - 2 (q1^2 + q2^2)
+// each evaluated as written, one rounded operation at a time.  R is stored
+// row-major, 9 values per quaternion.  The zero quaternion gives
+// q^ = (0, 0, 1, 0), the half turn about the third axis.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rotation(const T* __restrict__ q, T* __restrict__ R, T* norm,
+                                                   int64_t count) {
+  using F = FP<T>;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    T x[4], u[4], r, h;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) x[k] = q[i * 4 + k];
+    normalize_small<T, 4>(x, u, r, h, true);
+    if (norm) norm[i] = r;
+    const T q1 = u[0], q2 = u[1], q3 = u[2], q4 = u[3];
+    const T two = T(2), one = T(1);
+    const T q11 = F::mul(q1, q1), q22 = F::mul(q2, q2), q33 = F::mul(q3, q3);
+    const T q12 = F::mul(q1, q2), q13 = F::mul(q1, q3), q23 = F::mul(q2, q3);
+    const T q14 = F::mul(q1, q4), q24 = F::mul(q2, q4), q34 = F::mul(q3, q4);
+    T* o = R + i * 9;
+    o[0] = F::sub(one, F::mul(two, F::add(q22, q33)));
+    o[1] = F::mul(two, F::sub(q12, q34));
+    o[2] = F::mul(two, F::add(q13, q24));
+    o[3] = F::mul(two, F::add(q12, q34));
+    o[4] = F::sub(one, F::mul(two, F::add(q11, q33)));
+    o[5] = F::mul(two, F::sub(q23, q14));
+    o[6] = F::mul(two, F::sub(q13, q24));
+    o[7] = F::mul(two, F::add(q23, q14));
+    o[8] = F::sub(one, F::mul(two, F::add(q11, q22)));
+  }
+}
+
+template <typename T>
+cudaError_t launch_rotation(const T* q, T* R, T* norm, int64_t count, cudaStream_t s) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rotation<T>, 256, 0);
+  int64_t need = (count + 255) / 256;
+  int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
+  k_rotation<T><<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(q, R, norm, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_rotation<float>(const float*, float*, float*, int64_t, cudaStream_t);
+template cudaError_t launch_rotation<double>(const double*, double*, double*, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Measurement aid: a streaming copy with 16-byte loads and stores, the
+// achievable bandwidth ceiling for the same bytes.
+__global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n16; i0 += stride * U) {
+    uint4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * stride < n16) v[u] = __ldcs(src + i0 + u * stride);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (i0 + u * stride < n16) __stcs(dst + i0 + u * stride, v[u]);
+  }
+}
+
+__global__ void k_copy1(const unsigned char* __restrict__ src, unsigned char* __restrict__ dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s) {
+  const bool al = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) == 0 &&
+                  (bytes % 16) == 0;
+  int per_sm = 0;
+  if (al) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_copy16, 256, 0);
+    const int64_t n16 = bytes / 16;
+    int64_t need = (n16 + 1023) / 1024;
+    int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
+    k_copy16<<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(
+        reinterpret_cast<const uint4*>(src), reinterpret_cast<uint4*>(dst), n16);
+  } else {
+    k_copy1<<<device_sm_count() * 8, 256, 0, s>>>(reinterpret_cast<const unsigned char*>(src),
+                                                  reinterpret_cast<unsigned char*>(dst), bytes);
+  }
+  return cudaGetLastError();
+}
+
+// Measurement aid: the naive algorithm the paper compares with in Table 4,
+// y = x * (1 / sqrt(x1^2 + ... + xd^2)) with no scaling (it overflows and
+// underflows where the scaling algorithms do not), for d <= 4.
+template <typename T, int D>
+__global__ void __launch_bounds__(256) k_naive(const T* __restrict__ x, T* __restrict__ y, int64_t count, int vec) {
+  using F = FP<T>;
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+    T v[U][D];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
+        if constexpr (D * sizeof(T) == 16) {
+          if (vec) { Vec<T, D>::load(x + i * D, v[u]); continue; }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[u][k] = x[i * D + k];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
+        T s = F::mul(v[u][0], v[u][0]);
+#pragma unroll
+        for (int k = 1; k < D; ++k) s = F::add(s, F::mul(v[u][k], v[u][k]));
+        const T h = F::rcp(F::sqrt(s));
+        T o[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) o[k] = F::mul(h, v[u][k]);
+        if constexpr (D * sizeof(T) == 16) {
+          if (vec) { Vec<T, D>::store(y + i * D, o); continue; }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) y[i * D + k] = o[k];
+      }
+    }
+  }
+}
+
+template <typename T, int D>
+static cudaError_t launch_naive_d(const T* x, T* y, int64_t count, cudaStream_t s) {
+  const int vec = (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0) ? 1 : 0;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_naive<T, D>, 256, 0);
+  int64_t need = (count + 1023) / 1024;
+  int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
+  k_naive<T, D><<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(x, y, count, vec);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_naive(const T* x, T* y, int64_t count, int dim, cudaStream_t s) {
+  switch (dim) {
+    case 2: return launch_naive_d<T, 2>(x, y, count, s);
+    case 3: return launch_naive_d<T, 3>(x, y, count, s);
+    case 4: return launch_naive_d<T, 4>(x, y, count, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+template cudaError_t launch_naive<float>(const float*, float*, int64_t, int, cudaStream_t);
+template cudaError_t launch_naive<double>(const double*, double*, int64_t, int, cudaStream_t);
+
+}  // namespace ngb

@@ -1,0 +1,361 @@
+// kernels_fixed.cuh -- dense [count][dim] batches: forward and backward
+// kernels and their launchers, instantiated per precision by fixed_f32.cu and
+// fixed_f64.cu.
+//
+//   dim <= 4           one vector per thread (Algorithms 5-7); 16-byte vector
+//                      loads when a vector is 16 bytes (binary32 quaternions,
+//                      binary64 pairs), otherwise a 256-vector tile staged
+//                      through shared memory with 16-byte loads.
+//   5 <= dim <= 16     one vector per thread, order CR(n).
+//   17 <= dim <= 1024  one warp per row held in registers, 16-byte loads when
+//                      rows are 16-byte aligned.
+//   dim > 1024         one block per row (registers up to 4096, three passes
+//                      over the row beyond that).
+#pragma once
+#include "ngb_internal.h"
+#include "ngb_rowpath.cuh"
+
+namespace ngb {
+
+constexpr int SMALL_THREADS = 256;
+
+// ---------------------------------------------------------------------------
+// dim <= 4, one 16-byte vector per thread, U vectors in flight per thread.
+template <typename T, int D>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_vec16(const T* __restrict__ x, T* y, VecOut<T> out,
+                                                                int64_t count, int quat_zero) {
+  static_assert(D * sizeof(T) == 16, "one 16-byte vector per element vector");
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+    T xv[U][D];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) Vec<T, D>::load(x + i * D, xv[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
+        T yv[D], r, h;
+        const int code = normalize_small<T, D>(xv[u], yv, r, h, quat_zero != 0);
+        if (y) Vec<T, D>::store(y + i * D, yv);
+        out.put(i, r, h, code);
+      }
+    }
+  }
+}
+
+// dim <= 4, a tile of SMALL_THREADS vectors staged through shared memory
+// (16-byte loads and stores when x and y are 16-byte aligned).
+template <typename T, int D>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_staged(const T* __restrict__ x, T* y, VecOut<T> out,
+                                                                 int64_t count, int quat_zero, int vec16) {
+  constexpr int NT = SMALL_THREADS;
+  constexpr int W = 16 / sizeof(T);
+  constexpr int NC = NT * D / W;
+  __shared__ __align__(16) T tile[NT * D];
+  const int t = threadIdx.x;
+  for (int64_t v0 = (int64_t)blockIdx.x * NT; v0 < count; v0 += (int64_t)gridDim.x * NT) {
+    const int nv = (int)((count - v0) < NT ? (count - v0) : NT);
+    const T* src = x + v0 * D;
+    if (vec16 && nv == NT) {
+      for (int i = t; i < NC; i += NT)
+        reinterpret_cast<uint4*>(tile)[i] = __ldcs(reinterpret_cast<const uint4*>(src) + i);
+    } else {
+      for (int i = t; i < nv * D; i += NT) tile[i] = src[i];
+    }
+    __syncthreads();
+    T yv[D];
+    if (t < nv) {
+      T xv[D], r, h;
+#pragma unroll
+      for (int k = 0; k < D; ++k) xv[k] = tile[t * D + k];
+      const int code = normalize_small<T, D>(xv, yv, r, h, quat_zero != 0);
+      out.put(v0 + t, r, h, code);
+    }
+    __syncthreads();
+    if (y) {
+      if (t < nv) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) tile[t * D + k] = yv[k];
+      }
+      __syncthreads();
+      T* dst = y + v0 * D;
+      if (vec16 && nv == NT) {
+        for (int i = t; i < NC; i += NT)
+          __stcs(reinterpret_cast<uint4*>(dst) + i, reinterpret_cast<const uint4*>(tile)[i]);
+      } else {
+        for (int i = t; i < nv * D; i += NT) dst[i] = tile[i];
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template <typename T, int D>
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                              const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                              T* grad, int64_t count, int vec16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    T yv[D], gv[D], o[D];
+    bool done = false;
+    if constexpr (D * sizeof(T) == 16) {
+      if (vec16) {
+        Vec<T, D>::load(y + i * D, yv);
+        Vec<T, D>::load(g + i * D, gv);
+        backward_small<T, D>(yv, gv, hs[i], cs[i], o);
+        Vec<T, D>::store(grad + i * D, o);
+        done = true;
+      }
+    }
+    if (!done) {
+#pragma unroll
+      for (int k = 0; k < D; ++k) { yv[k] = y[i * D + k]; gv[k] = g[i * D + k]; }
+      backward_small<T, D>(yv, gv, hs[i], cs[i], o);
+#pragma unroll
+      for (int k = 0; k < D; ++k) grad[i * D + k] = o[k];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5 <= dim <= 16, one row per thread.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_thread(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
+                                                      int n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride) {
+    T r, h;
+    const int code = normalize_thread_generic<T, 16>(x + i * n, y ? y + i * n : nullptr, n, r, h);
+    out.put(i, r, h, code);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_thread_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                          const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                          T* grad, int64_t count, int n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    backward_thread_generic<T, 16>(y + i * n, g + i * n, n, hs[i], cs[i], grad + i * n);
+}
+
+// 17 <= dim <= 1024, one warp per row (grid-stride over rows).
+template <typename T, int V, int CH>
+__global__ void __launch_bounds__(256) k_rows_warp(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
+                                                    int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < count; row += nw)
+    warp_forward<T, V, CH>(x + row * n, y ? y + row * n : nullptr, n, lane, out, row);
+}
+
+template <typename T, int V, int CH>
+__global__ void __launch_bounds__(256) k_rows_warp_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                        const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                        T* grad, int64_t count, int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < count; row += nw)
+    warp_backward<T, V, CH>(y + row * n, g + row * n, grad + row * n, n, lane, hs[row], cs[row]);
+}
+
+// dim > 1024, one block per row (CH = 0: three passes over the row).
+template <typename T, int B, int CH>
+__global__ void __launch_bounds__(B) k_rows_block(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
+                                                   int n) {
+  __shared__ BlockShared<T, B> sh;
+  for (int64_t row = blockIdx.x; row < count; row += gridDim.x) {
+    if (CH > 0)
+      block_forward<T, B, (CH > 0 ? CH : 1)>(x + row * n, y ? y + row * n : nullptr, n, out, row, sh);
+    else
+      block_forward_stream<T, B>(x + row * n, y ? y + row * n : nullptr, n, out, row, sh);
+  }
+}
+
+template <typename T, int B, int CH>
+__global__ void __launch_bounds__(B) k_rows_block_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                       const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                       T* grad, int64_t count, int n) {
+  __shared__ BlockShared<T, B> sh;
+  for (int64_t row = blockIdx.x; row < count; row += gridDim.x) {
+    if (CH > 0)
+      block_backward<T, B, (CH > 0 ? CH : 1)>(y + row * n, g + row * n, grad + row * n, n, hs[row], cs[row], sh);
+    else
+      block_backward_stream<T, B>(y + row * n, g + row * n, grad + row * n, n, hs[row], cs[row], sh);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+inline bool aligned16(const void* p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+template <typename K>
+inline int grid_for(K kernel, int threads, int64_t work_items, int items_per_block) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t need = (work_items + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)device_sm_count() * per_sm;
+  if (need < 1) need = 1;
+  return (int)(need < cap ? need : cap);
+}
+
+template <typename T, int D>
+cudaError_t launch_small_fwd(const T* x, T* y, VecOut<T> out, int64_t count, bool quat_zero, cudaStream_t s) {
+  const bool vec16 = aligned16(x) && aligned16(y);
+  if constexpr (D * sizeof(T) == 16) {
+    if (vec16) {
+      auto k = k_small_vec16<T, D>;
+      const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS * 4);
+      k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero);
+      return cudaGetLastError();
+    }
+  }
+  {
+    auto k = k_small_staged<T, D>;
+    const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS);
+    k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero, vec16 ? 1 : 0);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int D>
+cudaError_t launch_small_bwd(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
+                             cudaStream_t s) {
+  const bool vec16 = aligned16(y) && aligned16(g) && aligned16(grad);
+  auto k = k_small_bwd<T, D>;
+  const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS * 4);
+  k<<<grid, SMALL_THREADS, 0, s>>>(y, g, h, c, grad, count, vec16 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+// Number of 32*V-element chunks per lane: the smallest power of two covering n.
+inline int chunks_for(int n, int per_chunk) {
+  int ch = 1;
+  while (ch * per_chunk < n) ch *= 2;
+  return ch;
+}
+
+template <typename T, int V, int CH>
+cudaError_t launch_warp_rows(const T* x, T* y, VecOut<T> out, int64_t count, int n, cudaStream_t s) {
+  auto k = k_rows_warp<T, V, CH>;
+  const int grid = grid_for(k, 256, count, 8);
+  k<<<grid, 256, 0, s>>>(x, y, out, count, n);
+  return cudaGetLastError();
+}
+
+template <typename T, int V, int CH>
+cudaError_t launch_warp_rows_bwd(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count, int n,
+                                 cudaStream_t s) {
+  auto k = k_rows_warp_bwd<T, V, CH>;
+  const int grid = grid_for(k, 256, count, 8);
+  k<<<grid, 256, 0, s>>>(y, g, h, c, grad, count, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t count, int dim, bool quat_zero,
+                                      cudaStream_t s) {
+  constexpr int W = 16 / sizeof(T);
+  switch (dim) {
+    case 1: return launch_small_fwd<T, 1>(x, y, out, count, false, s);
+    case 2: return launch_small_fwd<T, 2>(x, y, out, count, false, s);
+    case 3: return launch_small_fwd<T, 3>(x, y, out, count, false, s);
+    case 4: return launch_small_fwd<T, 4>(x, y, out, count, quat_zero, s);
+    default: break;
+  }
+  if (dim <= 16) {
+    auto k = k_rows_thread<T>;
+    const int grid = grid_for(k, 256, count, 256);
+    k<<<grid, 256, 0, s>>>(x, y, out, count, dim);
+    return cudaGetLastError();
+  }
+  if (dim <= CR_SLOTS) {
+    const bool vec = (dim % W == 0) && aligned16(x) && aligned16(y);
+    if (vec) {
+      switch (chunks_for(dim, 32 * W)) {
+        case 1: return launch_warp_rows<T, W, 1>(x, y, out, count, dim, s);
+        case 2: return launch_warp_rows<T, W, 2>(x, y, out, count, dim, s);
+        case 4: return launch_warp_rows<T, W, 4>(x, y, out, count, dim, s);
+        case 8: return launch_warp_rows<T, W, 8>(x, y, out, count, dim, s);
+        default: return launch_warp_rows<T, W, 32 / W>(x, y, out, count, dim, s);
+      }
+    }
+    switch (chunks_for(dim, 32)) {
+      case 1: return launch_warp_rows<T, 1, 1>(x, y, out, count, dim, s);
+      case 2: return launch_warp_rows<T, 1, 2>(x, y, out, count, dim, s);
+      case 4: return launch_warp_rows<T, 1, 4>(x, y, out, count, dim, s);
+      case 8: return launch_warp_rows<T, 1, 8>(x, y, out, count, dim, s);
+      case 16: return launch_warp_rows<T, 1, 16>(x, y, out, count, dim, s);
+      default: return launch_warp_rows<T, 1, 32>(x, y, out, count, dim, s);
+    }
+  }
+  if (dim <= 256 * 8) {
+    auto k = k_rows_block<T, 256, 8>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
+  } else if (dim <= 256 * 16) {
+    auto k = k_rows_block<T, 256, 16>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
+  } else {
+    auto k = k_rows_block<T, 256, 0>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
+                                       int dim, cudaStream_t s) {
+  constexpr int W = 16 / sizeof(T);
+  switch (dim) {
+    case 1: return launch_small_bwd<T, 1>(y, g, h, c, grad, count, s);
+    case 2: return launch_small_bwd<T, 2>(y, g, h, c, grad, count, s);
+    case 3: return launch_small_bwd<T, 3>(y, g, h, c, grad, count, s);
+    case 4: return launch_small_bwd<T, 4>(y, g, h, c, grad, count, s);
+    default: break;
+  }
+  if (dim <= 16) {
+    auto k = k_rows_thread_bwd<T>;
+    k<<<grid_for(k, 256, count, 256), 256, 0, s>>>(y, g, h, c, grad, count, dim);
+    return cudaGetLastError();
+  }
+  if (dim <= CR_SLOTS) {
+    const bool vec = (dim % W == 0) && aligned16(y) && aligned16(g) && aligned16(grad);
+    if (vec) {
+      switch (chunks_for(dim, 32 * W)) {
+        case 1: return launch_warp_rows_bwd<T, W, 1>(y, g, h, c, grad, count, dim, s);
+        case 2: return launch_warp_rows_bwd<T, W, 2>(y, g, h, c, grad, count, dim, s);
+        case 4: return launch_warp_rows_bwd<T, W, 4>(y, g, h, c, grad, count, dim, s);
+        case 8: return launch_warp_rows_bwd<T, W, 8>(y, g, h, c, grad, count, dim, s);
+        default: return launch_warp_rows_bwd<T, W, 32 / W>(y, g, h, c, grad, count, dim, s);
+      }
+    }
+    switch (chunks_for(dim, 32)) {
+      case 1: return launch_warp_rows_bwd<T, 1, 1>(y, g, h, c, grad, count, dim, s);
+      case 2: return launch_warp_rows_bwd<T, 1, 2>(y, g, h, c, grad, count, dim, s);
+      case 4: return launch_warp_rows_bwd<T, 1, 4>(y, g, h, c, grad, count, dim, s);
+      case 8: return launch_warp_rows_bwd<T, 1, 8>(y, g, h, c, grad, count, dim, s);
+      case 16: return launch_warp_rows_bwd<T, 1, 16>(y, g, h, c, grad, count, dim, s);
+      default: return launch_warp_rows_bwd<T, 1, 32>(y, g, h, c, grad, count, dim, s);
+    }
+  }
+  if (dim <= 256 * 8) {
+    auto k = k_rows_block_bwd<T, 256, 8>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
+  } else if (dim <= 256 * 16) {
+    auto k = k_rows_block_bwd<T, 256, 16>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
+  } else {
+    auto k = k_rows_block_bwd<T, 256, 0>;
+    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ngb

@@ -1,0 +1,303 @@
+// kernels_ragged.cuh -- ragged batches (vector i = x[offsets[i] .. offsets[i+1]))
+// in one persistent launch, forward and backward; instantiated per precision
+// by ragged_f32.cu and ragged_f64.cu.
+//
+// 1. k_classify reads the int64 offsets once, skips (and flags) vectors with
+//    bad offsets, finishes zero-length vectors (norm +0), and appends every
+//    other vector index to one of three lists by length: the block list
+//    (n > warp_max), the warp list (thread_max < n <= warp_max) and the thread
+//    list (n <= thread_max).  Appends are aggregated per block: one atomic per
+//    block and list.
+// 2. k_ragged_fwd / k_ragged_bwd run one wave of persistent blocks that take
+//    work from the three lists in that order (longest vectors first) through
+//    atomic tickets, whole blocks on block items, warps on batches of warp
+//    items, lanes on thread items.  No block ever waits for another.
+// Every mapping evaluates the same operations in the same order (the paper's
+// Algorithms 3-7 for n <= 4, the order CR(n) for n >= 5), so the results do
+// not depend on the mapping, the grid or the order in which items are taken.
+#pragma once
+#include "ngb_internal.h"
+#include "ngb_rowpath.cuh"
+
+namespace ngb {
+
+constexpr int CLASSIFY_THREADS = 1024;
+constexpr int WARP_BATCH = 4;     // warp items per ticket
+constexpr int THREAD_BATCH = 4;   // 32-item groups per ticket
+
+template <typename T>
+__global__ void __launch_bounds__(CLASSIFY_THREADS)
+    k_classify(const int64_t* __restrict__ off, int64_t count, int64_t capacity, int thread_max, int warp_max,
+               int validate, RaggedScratch sc, VecOut<T> zero_out) {
+  __shared__ int wcount[CLASSIFY_THREADS / 32][3];
+  __shared__ int wbase[CLASSIFY_THREADS / 32][3];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int64_t base = (int64_t)blockIdx.x * CLASSIFY_THREADS; base < count;
+       base += (int64_t)gridDim.x * CLASSIFY_THREADS) {
+    const int64_t i = base + t;
+    int b = -1;
+    if (i < count) {
+      const int64_t s = off[i], e = off[i + 1];
+      const int64_t n = e - s;
+      const bool bad = n < 0 || n > MAX_LEN || s < 0 || (capacity > 0 && e > capacity) ||
+                       (validate && i == 0 && s != 0);
+      if (bad) {
+        atomicOr(sc.status, 1);
+      } else if (n == 0) {
+        zero_out.put(i, T(0), T(0), CODE_ZERO);
+      } else {
+        // n <= 4 always runs Algorithms 5-7 in one thread
+        b = (n <= thread_max || n <= 4) ? 2 : (n <= warp_max ? 1 : 0);
+      }
+    }
+    unsigned ball[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      ball[k] = __ballot_sync(FULL, b == k);
+      if (lane == 0) wcount[w][k] = __popc(ball[k]);
+    }
+    __syncthreads();
+    if (t < 3) {
+      int sum = 0;
+      for (int ww = 0; ww < CLASSIFY_THREADS / 32; ++ww) {
+        const int c = wcount[ww][t];
+        wbase[ww][t] = sum;
+        sum += c;
+      }
+      const int g = sum ? atomicAdd(&sc.counts[t], sum) : 0;
+      for (int ww = 0; ww < CLASSIFY_THREADS / 32; ++ww) wbase[ww][t] += g;
+    }
+    __syncthreads();
+    if (b >= 0) {
+      const unsigned mine = b == 0 ? ball[0] : (b == 1 ? ball[1] : ball[2]);
+      sc.items[(int64_t)b * count + wbase[w][b] + __popc(mine & lt_mask)] = (int32_t)i;
+    }
+    __syncthreads();
+  }
+}
+
+// One vector of n <= 16 components by one thread (vector zero rule for n = 4).
+template <typename T>
+__device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr, int n, const VecOut<T>& out,
+                                                int64_t vec) {
+  T r, h;
+  int code;
+  if (n <= 4) {
+    T xv[4], yv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = k < n ? xr[k] : T(0);
+    switch (n) {
+      case 1: code = normalize_small<T, 1>(xv, yv, r, h, false); break;
+      case 2: code = normalize_small<T, 2>(xv, yv, r, h, false); break;
+      case 3: code = normalize_small<T, 3>(xv, yv, r, h, false); break;
+      default: code = normalize_small<T, 4>(xv, yv, r, h, false); break;
+    }
+    if (yr) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < n) yr[k] = yv[k];
+    }
+  } else {
+    code = normalize_thread_generic<T, 16>(xr, yr, n, r, h);
+  }
+  out.put(vec, r, h, code);
+}
+
+template <typename T>
+__device__ __forceinline__ void thread_item_bwd(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
+                                                T h, int code) {
+  if (n <= 4) {
+    T yv[4], gv[4], o[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      yv[k] = k < n ? yr[k] : T(0);
+      gv[k] = k < n ? gr[k] : T(0);
+    }
+    switch (n) {
+      case 1: backward_small<T, 1>(yv, gv, h, code, o); break;
+      case 2: backward_small<T, 2>(yv, gv, h, code, o); break;
+      case 3: backward_small<T, 3>(yv, gv, h, code, o); break;
+      default: backward_small<T, 4>(yv, gv, h, code, o); break;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < n) gradr[k] = o[k];
+  } else {
+    backward_thread_generic<T, 16>(yr, gr, n, h, code, gradr);
+  }
+}
+
+template <typename T, int WCH>
+__device__ __forceinline__ void warp_item_fwd(const T* __restrict__ xr, T* yr, int n, int lane, const VecOut<T>& out,
+                                              int64_t vec) {
+  if (n <= 32) warp_forward<T, 1, 1>(xr, yr, n, lane, out, vec);
+  else if (n <= 64) warp_forward<T, 1, 2>(xr, yr, n, lane, out, vec);
+  else if (n <= 128) warp_forward<T, 1, 4>(xr, yr, n, lane, out, vec);
+  else if (n <= 256 || WCH <= 8) warp_forward<T, 1, (WCH < 8 ? WCH : 8)>(xr, yr, n, lane, out, vec);
+  else if (n <= 512 || WCH <= 16) warp_forward<T, 1, (WCH < 16 ? WCH : 16)>(xr, yr, n, lane, out, vec);
+  else warp_forward<T, 1, WCH>(xr, yr, n, lane, out, vec);
+}
+
+template <typename T, int WCH>
+__device__ __forceinline__ void warp_item_bwd(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
+                                              int lane, T h, int code) {
+  if (n <= 32) warp_backward<T, 1, 1>(yr, gr, gradr, n, lane, h, code);
+  else if (n <= 64) warp_backward<T, 1, 2>(yr, gr, gradr, n, lane, h, code);
+  else if (n <= 128) warp_backward<T, 1, 4>(yr, gr, gradr, n, lane, h, code);
+  else if (n <= 256 || WCH <= 8) warp_backward<T, 1, (WCH < 8 ? WCH : 8)>(yr, gr, gradr, n, lane, h, code);
+  else if (n <= 512 || WCH <= 16) warp_backward<T, 1, (WCH < 16 ? WCH : 16)>(yr, gr, gradr, n, lane, h, code);
+  else warp_backward<T, 1, WCH>(yr, gr, gradr, n, lane, h, code);
+}
+
+template <typename T>
+struct RaggedArgs {
+  const T* x;          // forward input, or y for the backward pass
+  T* y;                // forward output (nullable: norm only), or grad
+  const T* g;          // backward: upstream gradient
+  const T* h_in;       // backward: saved h
+  const int8_t* c_in;  // backward: saved code
+  VecOut<T> out;       // forward per-vector outputs
+  const int64_t* off;
+  RaggedScratch sc;
+  int64_t count;
+};
+
+// WCH: chunks of 32 per lane for warp items (warp_max <= 32 WCH).
+template <typename T, int B, int WCH, bool BWD>
+__global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
+  __shared__ BlockShared<T, B> sh;
+  const int t = threadIdx.x, lane = t & 31;
+  const int nblk = a.sc.counts[0], nwarp = a.sc.counts[1], nthr = a.sc.counts[2];
+  const int32_t* Lb = a.sc.items;
+  const int32_t* Lw = a.sc.items + a.count;
+  const int32_t* Lt = a.sc.items + 2 * a.count;
+
+  // block items, one ticket per item
+  for (;;) {
+    if (t == 0) sh.item = atomicAdd(&a.sc.tickets[0], 1);
+    __syncthreads();
+    const int it = sh.item;
+    __syncthreads();
+    if (it >= nblk) break;
+    const int64_t vec = Lb[it];
+    const int64_t s = a.off[vec];
+    const int n = (int)(a.off[vec + 1] - s);
+    if constexpr (!BWD) {
+      T* yr = a.y ? a.y + s : nullptr;
+      if (n <= 8 * B) block_forward<T, B, 8>(a.x + s, yr, n, a.out, vec, sh);
+      else if (n <= 16 * B) block_forward<T, B, 16>(a.x + s, yr, n, a.out, vec, sh);
+      else block_forward_stream<T, B>(a.x + s, yr, n, a.out, vec, sh);
+    } else {
+      const T h = a.h_in[vec];
+      const int code = a.c_in[vec];
+      if (n <= 8 * B) block_backward<T, B, 8>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+      else if (n <= 16 * B) block_backward<T, B, 16>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+      else block_backward_stream<T, B>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+    }
+  }
+
+  // warp items, WARP_BATCH per ticket
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.sc.tickets[1], WARP_BATCH);
+    base = __shfl_sync(FULL, base, 0);
+    if (base >= nwarp) break;
+    for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
+      const int64_t vec = Lw[base + j];
+      const int64_t s = a.off[vec];
+      const int n = (int)(a.off[vec + 1] - s);
+      if constexpr (!BWD) {
+        warp_item_fwd<T, WCH>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+      } else {
+        warp_item_bwd<T, WCH>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
+      }
+    }
+  }
+
+  // thread items, THREAD_BATCH groups of 32 per ticket
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.sc.tickets[2], 32 * THREAD_BATCH);
+    base = __shfl_sync(FULL, base, 0);
+    if (base >= nthr) break;
+#pragma unroll 1
+    for (int j = 0; j < THREAD_BATCH; ++j) {
+      const int it = base + 32 * j + lane;
+      if (it < nthr) {
+        const int64_t vec = Lt[it];
+        const int64_t s = a.off[vec];
+        const int n = (int)(a.off[vec + 1] - s);
+        if constexpr (!BWD) {
+          thread_item_fwd<T>(a.x + s, a.y ? a.y + s : nullptr, n, a.out, vec);
+        } else {
+          thread_item_bwd<T>(a.x + s, a.g + s, a.y + s, n, a.h_in[vec], a.c_in[vec]);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int B, int WCH, bool BWD>
+inline int full_wave_of() {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ragged<T, B, WCH, BWD>, B, 0);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * device_sm_count();
+}
+
+template <typename T, bool BWD>
+inline int full_wave_dispatch(const RaggedMapping& m) {
+  const bool big = m.warp_max > 512;
+  if (m.block_threads == 512) return big ? full_wave_of<T, 512, 32, BWD>() : full_wave_of<T, 512, 16, BWD>();
+  return big ? full_wave_of<T, 256, 32, BWD>() : full_wave_of<T, 256, 16, BWD>();
+}
+
+template <typename T, bool BWD>
+inline void launch_persistent(const RaggedArgs<T>& a, const RaggedMapping& m, cudaStream_t s) {
+  const int grid = m.grid_blocks > 0 ? m.grid_blocks : full_wave_dispatch<T, BWD>(m);
+  const bool big = m.warp_max > 512;
+  if (m.block_threads == 512) {
+    if (big) k_ragged<T, 512, 32, BWD><<<grid, 512, 0, s>>>(a);
+    else k_ragged<T, 512, 16, BWD><<<grid, 512, 0, s>>>(a);
+  } else {
+    if (big) k_ragged<T, 256, 32, BWD><<<grid, 256, 0, s>>>(a);
+    else k_ragged<T, 256, 16, BWD><<<grid, 256, 0, s>>>(a);
+  }
+}
+
+template <typename T>
+cudaError_t launch_ragged_impl(const T* x, T* y, T* norm, T* saved_h, int8_t* saved_code, const T* g, const T* h_in,
+                               const int8_t* code_in, T* grad, const int64_t* offsets, int64_t count,
+                               int64_t capacity, bool validate, const RaggedMapping& map, const RaggedScratch& sc,
+                               bool backward, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(sc.counts, 0, 6 * sizeof(int32_t), s);  // counts and tickets are adjacent
+  if (e != cudaSuccess) return e;
+  {
+    const int64_t blocks_needed = (count + CLASSIFY_THREADS - 1) / CLASSIFY_THREADS;
+    const int64_t cap = (int64_t)device_sm_count() * 2;
+    const int grid = (int)(blocks_needed < cap ? (blocks_needed > 0 ? blocks_needed : 1) : cap);
+    VecOut<T> zo = backward ? VecOut<T>{nullptr, nullptr, nullptr} : VecOut<T>{norm, saved_h, saved_code};
+    k_classify<T><<<grid, CLASSIFY_THREADS, 0, s>>>(offsets, count, capacity, map.thread_max, map.warp_max,
+                                                     validate ? 1 : 0, sc, zo);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  RaggedArgs<T> a;
+  a.off = offsets;
+  a.sc = sc;
+  a.count = count;
+  if (!backward) {
+    a.x = x; a.y = y; a.g = nullptr; a.h_in = nullptr; a.c_in = nullptr;
+    a.out = VecOut<T>{norm, saved_h, saved_code};
+    launch_persistent<T, false>(a, map, s);
+  } else {
+    a.x = x; a.y = grad; a.g = g; a.h_in = h_in; a.c_in = code_in;
+    a.out = VecOut<T>{nullptr, nullptr, nullptr};
+    launch_persistent<T, true>(a, map, s);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ngb

@@ -1,0 +1,296 @@
+// ngb_arith.cuh -- device arithmetic of the scaling normalization of
+// Mascarenhas, "Fast and accurate normalization of vectors and quaternions"
+// (arXiv 1606.06508), as inline device functions shared by every kernel.
+//
+// Every floating-point step is one correctly rounded IEEE operation through
+// the __*_rn intrinsics (round to nearest even, never contracted into a fused
+// multiply-add), and the library is built with -ftz=false -prec-div=true
+// -prec-sqrt=true -fmad=false: the error analysis of the paper assumes IEEE
+// arithmetic with gradual underflow (Section 3, remark on DAZ/FTZ).  The
+// operations run in the order of Algorithms 3-7 so that results are
+// bit-identical to a sequential evaluation of the same steps.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ngb {
+
+enum : int { CODE_ONE = 0, CODE_SIGMA_MIN = 1, CODE_SIGMA_MAX = 2, CODE_ZERO = 3 };
+
+// Canonical summation order for n >= 5: CR_SLOTS slots, slot j holding the
+// left-to-right sum of terms j, j + CR_SLOTS, ...; then a halving tree over
+// the slots with strides CR_SLOTS/2 .. 1, skipping slots that hold no term.
+constexpr int CR_SLOTS = 1024;
+constexpr int MAX_LEN = 1 << 20;
+
+template <typename T> struct FP;
+
+template <> struct FP<float> {
+  __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+  __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+  __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ __forceinline__ static float sqrt(float a) { return __fsqrt_rn(a); }
+  __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
+  __device__ __forceinline__ static float abs(float a) { return fabsf(a); }
+  __device__ __forceinline__ static float fmax(float a, float b) { return fmaxf(a, b); }
+  // Table 2, binary32 row (n <= 4)
+  static constexpr float tau_min = 0x1p-49f, sigma_min = 0x1p100f, inv_sigma_min = 0x1p-100f;
+  static constexpr float tau_max = 0x1p62f, sigma_max = 0x1p-66f, inv_sigma_max = 0x1p66f;
+  // 5 <= n <= 2^20: tau_max = 2^floor((log2(omega) - 21) / 2), sigma_max * omega <= tau_max
+  static constexpr float tau_max_n = 0x1p53f, sigma_max_n = 0x1p-75f, inv_sigma_max_n = 0x1p75f;
+};
+
+template <> struct FP<double> {
+  __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+  __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+  __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ __forceinline__ static double sqrt(double a) { return __dsqrt_rn(a); }
+  __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
+  __device__ __forceinline__ static double abs(double a) { return fabs(a); }
+  __device__ __forceinline__ static double fmax(double a, double b) { return ::fmax(a, b); }
+  // Table 2, binary64 row (n <= 4)
+  static constexpr double tau_min = 0x1p-482, sigma_min = 0x1p592, inv_sigma_min = 0x1p-592;
+  static constexpr double tau_max = 0x1p510, sigma_max = 0x1p-514, inv_sigma_max = 0x1p514;
+  static constexpr double tau_max_n = 0x1p501, sigma_max_n = 0x1p-523, inv_sigma_max_n = 0x1p523;
+};
+
+// The factor choice of Scale2D/Scale3D/Normalize4D: compare the largest
+// magnitude m with tau_min and tau_max.  A NaN m fails both comparisons and
+// takes the sigma_min branch, as in the paper.
+template <typename T, bool GENERIC>
+__device__ __forceinline__ int select_code(T m) {
+  const T tmax = GENERIC ? FP<T>::tau_max_n : FP<T>::tau_max;
+  if (m >= FP<T>::tau_min) {
+    if (m <= tmax) return CODE_ONE;
+    return CODE_SIGMA_MAX;
+  }
+  return CODE_SIGMA_MIN;
+}
+
+// c, the factor applied to x (x~ = c x)
+template <typename T, bool GENERIC>
+__device__ __forceinline__ T factor_of(int code) {
+  const T smax = GENERIC ? FP<T>::sigma_max_n : FP<T>::sigma_max;
+  return code == CODE_SIGMA_MIN ? FP<T>::sigma_min : (code == CODE_SIGMA_MAX ? smax : T(1));
+}
+
+// sigma = 1/c, the first value returned by Scale2D/Scale3D (r^ = sigma r~)
+template <typename T, bool GENERIC>
+__device__ __forceinline__ T inverse_of(int code) {
+  const T ismax = GENERIC ? FP<T>::inv_sigma_max_n : FP<T>::inv_sigma_max;
+  return code == CODE_SIGMA_MIN ? FP<T>::inv_sigma_min : (code == CODE_SIGMA_MAX ? ismax : T(1));
+}
+
+// x~ = c x; with c = 1 the input is used as it is (as the algorithms return x).
+template <typename T>
+__device__ __forceinline__ T scale_by(int code, T c, T x) {
+  return code == CODE_ONE ? x : FP<T>::mul(c, x);
+}
+
+// ---------------------------------------------------------------------------
+// The largest magnitude of n <= 4 components in the branch order of Scale2D
+// (Algorithm 3), Scale3D (Algorithm 4) and Normalize4D (Algorithm 7).
+// Returns true for the zero result.  Readings: in Normalize4D the assignment
+// m <- |x4| belongs to an omitted Else; the zero result needs every component
+// equal to zero (in the branches that reach "m = 0" the components that were
+// not compared with ">=" may still be NaN, and a NaN input must give NaN).
+template <typename T, int D> struct SmallMax;
+
+template <typename T> struct SmallMax<T, 1> {
+  __device__ __forceinline__ static bool run(const T* x, T& m) {
+    m = FP<T>::abs(x[0]);
+    return m == T(0);
+  }
+};
+
+template <typename T> struct SmallMax<T, 2> {
+  __device__ __forceinline__ static bool run(const T* x, T& m) {
+    m = FP<T>::abs(x[0]);
+    if (m >= FP<T>::abs(x[1])) {
+      if (m == T(0)) return true;
+    } else {
+      m = FP<T>::abs(x[1]);
+    }
+    return false;
+  }
+};
+
+template <typename T> struct SmallMax<T, 3> {
+  __device__ __forceinline__ static bool run(const T* x, T& m) {
+    m = FP<T>::abs(x[0]);
+    if (m < FP<T>::abs(x[1])) {
+      m = FP<T>::abs(x[1]);
+      if (m < FP<T>::abs(x[2])) m = FP<T>::abs(x[2]);
+    } else {
+      if (m >= FP<T>::abs(x[2])) {
+        if (m == T(0) && x[1] == T(0)) return true;
+      } else {
+        m = FP<T>::abs(x[2]);
+      }
+    }
+    return false;
+  }
+};
+
+template <typename T> struct SmallMax<T, 4> {
+  __device__ __forceinline__ static bool run(const T* x, T& m) {
+    m = FP<T>::abs(x[0]);
+    if (m < FP<T>::abs(x[1])) {
+      m = FP<T>::abs(x[1]);
+      if (m < FP<T>::abs(x[2])) m = FP<T>::abs(x[2]);
+      if (m < FP<T>::abs(x[3])) m = FP<T>::abs(x[3]);
+    } else {
+      if (m < FP<T>::abs(x[2])) {
+        m = FP<T>::abs(x[2]);
+        if (m < FP<T>::abs(x[3])) m = FP<T>::abs(x[3]);
+      } else {
+        if (m >= FP<T>::abs(x[3])) {
+          if (m == T(0) && x[1] == T(0) && x[2] == T(0)) return true;
+        } else {
+          m = FP<T>::abs(x[3]);
+        }
+      }
+    }
+    return false;
+  }
+};
+
+// Normalize2D / Normalize3D / Normalize4D (Algorithms 5-7; n = 1 runs the same
+// steps on one component).  x and y may be the same array.  quat_zero picks
+// the [0, 0, 1, 0] zero result of Algorithm 7 for D = 4.
+// Returns the factor code; r = sigma r~, h = 1/r~.
+template <typename T, int D>
+__device__ __forceinline__ int normalize_small(const T* x, T* y, T& r, T& h, bool quat_zero) {
+  T m;
+  if (SmallMax<T, D>::run(x, m)) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) y[k] = T(0);
+    if (D == 4 && quat_zero) y[2] = T(1);
+    r = T(0);
+    h = T(0);
+    return CODE_ZERO;
+  }
+  const int code = select_code<T, false>(m);
+  const T c = factor_of<T, false>(code);
+  T t[D];
+#pragma unroll
+  for (int k = 0; k < D; ++k) t[k] = scale_by(code, c, x[k]);
+  T s = FP<T>::mul(t[0], t[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) s = FP<T>::add(s, FP<T>::mul(t[k], t[k]));
+  const T rt = FP<T>::sqrt(s);
+  h = FP<T>::rcp(rt);
+  r = FP<T>::mul(inverse_of<T, false>(code), rt);
+#pragma unroll
+  for (int k = 0; k < D; ++k) y[k] = FP<T>::mul(h, t[k]);
+  return code;
+}
+
+// Backward of y = x/|x| for n <= 4: dot = y.g left to right,
+// grad_k = ((g_k - y_k dot) h) c; zero input -> grad = +0.
+template <typename T, int D>
+__device__ __forceinline__ void backward_small(const T* y, const T* g, T h, int code, T* grad) {
+  if (code == CODE_ZERO) {
+#pragma unroll
+    for (int k = 0; k < D; ++k) grad[k] = T(0);
+    return;
+  }
+  const T c = factor_of<T, false>(code);
+  T dot = FP<T>::mul(y[0], g[0]);
+#pragma unroll
+  for (int k = 1; k < D; ++k) dot = FP<T>::add(dot, FP<T>::mul(y[k], g[k]));
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    const T tk = FP<T>::sub(g[k], FP<T>::mul(y[k], dot));
+    grad[k] = FP<T>::mul(FP<T>::mul(tk, h), c);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One thread, 5 <= n <= NMAX (NMAX <= CR_SLOTS): the generic steps with the
+// order CR(n), every slot holding one term.
+template <typename T, int NMAX>
+__device__ __forceinline__ T cr_sum_thread(T (&q)[NMAX], int n) {
+#pragma unroll
+  for (int s = NMAX / 2; s >= 1; s /= 2) {
+#pragma unroll
+    for (int j = 0; j < s; ++j)
+      if (j + s < n) q[j] = FP<T>::add(q[j], q[j + s]);
+  }
+  return q[0];
+}
+
+template <typename T, int NMAX>
+__device__ __forceinline__ int normalize_thread_generic(const T* __restrict__ xr, T* yr, int n, T& r, T& h) {
+  T v[NMAX];
+  bool nz = false;
+  T m = T(0);
+#pragma unroll
+  for (int k = 0; k < NMAX; ++k) {
+    v[k] = k < n ? xr[k] : T(0);
+    if (k < n) {
+      nz |= !(v[k] == T(0));
+      m = FP<T>::fmax(m, FP<T>::abs(v[k]));
+    }
+  }
+  if (!nz) {
+    if (yr)
+      for (int k = 0; k < n; ++k) yr[k] = T(0);
+    r = T(0);
+    h = T(0);
+    return CODE_ZERO;
+  }
+  const int code = select_code<T, true>(m);
+  const T c = factor_of<T, true>(code);
+  T q[NMAX];
+#pragma unroll
+  for (int k = 0; k < NMAX; ++k) {
+    v[k] = scale_by(code, c, v[k]);
+    q[k] = FP<T>::mul(v[k], v[k]);
+  }
+  const T rt = FP<T>::sqrt(cr_sum_thread<T, NMAX>(q, n));
+  h = FP<T>::rcp(rt);
+  r = FP<T>::mul(inverse_of<T, true>(code), rt);
+  if (yr) {
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k)
+      if (k < n) yr[k] = FP<T>::mul(h, v[k]);
+  }
+  return code;
+}
+
+template <typename T, int NMAX>
+__device__ __forceinline__ void backward_thread_generic(const T* __restrict__ yr, const T* __restrict__ gr, int n,
+                                                        T h, int code, T* gradr) {
+  if (code == CODE_ZERO) {
+    for (int k = 0; k < n; ++k) gradr[k] = T(0);
+    return;
+  }
+  const T c = factor_of<T, true>(code);
+  T yv[NMAX], gv[NMAX], q[NMAX];
+#pragma unroll
+  for (int k = 0; k < NMAX; ++k) {
+    yv[k] = k < n ? yr[k] : T(0);
+    gv[k] = k < n ? gr[k] : T(0);
+    q[k] = FP<T>::mul(yv[k], gv[k]);
+  }
+  const T dot = cr_sum_thread<T, NMAX>(q, n);
+#pragma unroll
+  for (int k = 0; k < NMAX; ++k)
+    if (k < n) gradr[k] = FP<T>::mul(FP<T>::mul(FP<T>::sub(gv[k], FP<T>::mul(yv[k], dot)), h), c);
+}
+
+// Per-vector outputs (each pointer nullable).
+template <typename T>
+struct VecOut {
+  T* norm;
+  T* saved_h;
+  int8_t* saved_code;
+  __device__ __forceinline__ void put(int64_t i, T r, T h, int code) const {
+    if (norm) norm[i] = r;
+    if (saved_h) saved_h[i] = h;
+    if (saved_code) saved_code[i] = (int8_t)code;
+  }
+};
+
+}  // namespace ngb

@@ -1,0 +1,55 @@
+// ngb_internal.h -- host-side declarations shared by the translation units of
+// the library (launchers, device properties, the ragged plan).  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ngb {
+
+template <typename T> struct VecOut;
+
+// Multiprocessor count of the current device (cached per device).
+int device_sm_count();
+
+// Dense [count][dim] batches.
+template <typename T>
+cudaError_t launch_fixed_forward(const T* x, T* y, T* norm, T* saved_h, int8_t* saved_code, int64_t count,
+                                 int dim, bool quat_zero, cudaStream_t s);
+template <typename T>
+cudaError_t launch_fixed_backward(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
+                                  int dim, cudaStream_t s);
+
+// Ragged batches: bucket lists produced by the classifier, consumed by one
+// persistent kernel.
+struct RaggedMapping {
+  int thread_max;     // n <= thread_max: one thread per vector (<= 16)
+  int warp_max;       // thread_max < n <= warp_max: one warp per vector (<= 1024)
+  int block_threads;  // n > warp_max: one block of this many threads per vector (256 or 512)
+  int grid_blocks;    // persistent grid size; 0 = one full wave
+};
+
+struct RaggedScratch {
+  int32_t* items;    // [3 * count]: block, warp and thread lists back to back
+  int32_t* counts;   // [3] items per list (filled by the classifier)
+  int32_t* tickets;  // [3] work counters of the persistent kernel
+  int32_t* status;   // bit 0: a vector with bad offsets was skipped
+};
+
+template <typename T>
+cudaError_t launch_ragged(const T* x, T* y, T* norm, T* saved_h, int8_t* saved_code, const T* g_or_null,
+                          const T* h_in, const int8_t* code_in, T* grad, const int64_t* offsets, int64_t count,
+                          int64_t capacity, bool validate, const RaggedMapping& map, const RaggedScratch& sc,
+                          bool backward, cudaStream_t s);
+
+// Grid of one full wave of the persistent ragged kernel for this mapping.
+template <typename T>
+int ragged_full_wave(const RaggedMapping& map, bool backward);
+
+// Measurement aids and extra entry points.
+cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
+template <typename T>
+cudaError_t launch_naive(const T* x, T* y, int64_t count, int dim, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rotation(const T* q, T* R, T* norm, int64_t count, cudaStream_t s);
+
+}  // namespace ngb

@@ -1,0 +1,464 @@
+// ngb_rowpath.cuh -- warp-per-vector and block-per-vector forms of the
+// generic (n >= 5) scaling normalization and of its backward pass.
+//
+// The sum of squares (and the backward dot product) follows the canonical
+// order CR(n): slot j < 1024 is the left-to-right sum of terms j, j + 1024, ...,
+// then slot j <- slot j + slot (j + s) for s = 512, 256, ..., 1 whenever slot
+// j + s holds a term.  Each mapping places the slots so that every tree level
+// becomes either an in-register add, a warp shuffle (xor by a power of two)
+// or one shared-memory exchange, and performs the levels in the same
+// descending order, so thread, warp and block mappings give identical bits.
+#pragma once
+#include "ngb_arith.cuh"
+
+namespace ngb {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ T warp_fmax(T m) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) m = FP<T>::fmax(m, __shfl_xor_sync(FULL, m, o));
+  return m;
+}
+
+// Streaming (evict-first) loads and stores of V consecutive elements.
+template <typename T, int V> struct Vec;
+template <typename T> struct Vec<T, 1> {
+  __device__ __forceinline__ static void load(const T* p, T* v) { v[0] = __ldcs(p); }
+  __device__ __forceinline__ static void store(T* p, const T* v) { __stcs(p, v[0]); }
+};
+template <> struct Vec<float, 4> {
+  __device__ __forceinline__ static void load(const float* p, float* v) {
+    float4 a = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  }
+  __device__ __forceinline__ static void store(float* p, const float* v) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+};
+template <> struct Vec<double, 2> {
+  __device__ __forceinline__ static void load(const double* p, double* v) {
+    double2 a = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = a.x; v[1] = a.y;
+  }
+  __device__ __forceinline__ static void store(double* p, const double* v) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(v[0], v[1]));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Warp layout.  Lane l holds chunk c (c < CH) as the V elements
+// k = 32 V c + V l + e, e < V.  Slot j = k for k < 1024, so with G = 1024/(32V)
+// chunk groups: strides >= 32V pair chunk c with c + s/(32V) inside a lane,
+// strides V .. 16V pair lane l with lane l ^ (s/V), and strides < V pair
+// element e with e + s inside a lane.  Elements k >= 1024 are added in
+// ascending order into the accumulator of chunk c mod G.
+// Requires n <= 32 V CH; for V > 1 also n % V == 0 and 16-byte aligned rows.
+template <typename T, int V, int CH>
+__device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
+  constexpr int G = CR_SLOTS / (32 * V);
+  constexpr int NS = CH < G ? CH : G;
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+  // slots with more than one term: sequential adds in ascending k
+#pragma unroll
+  for (int c = G; c < CH; ++c) {
+#pragma unroll
+    for (int e = 0; e < V; ++e)
+      if (32 * V * c + V * lane + e < n) q[c % G][e] = FP<T>::add(q[c % G][e], q[c][e]);
+  }
+  // strides 512 .. 32V: chunk c += chunk c + p
+#pragma unroll
+  for (int p = G / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int c = 0; c < p; ++c) {
+      if (c + p < NS) {
+#pragma unroll
+        for (int e = 0; e < V; ++e)
+          if (32 * V * (c + p) + V * lane + e < used) q[c][e] = FP<T>::add(q[c][e], q[c + p][e]);
+      }
+    }
+  }
+  // strides 16V .. V: lane l += lane l + p
+#pragma unroll
+  for (int p = 16; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      const T o = __shfl_xor_sync(FULL, q[0][e], p);
+      if (lane < p && V * (lane + p) + e < used) q[0][e] = FP<T>::add(q[0][e], o);
+    }
+  }
+  // strides V/2 .. 1 inside lane 0
+#pragma unroll
+  for (int p = V / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int e = 0; e < p; ++e)
+      if (e + p < used) q[0][e] = FP<T>::add(q[0][e], q[0][e + p]);
+  }
+  return __shfl_sync(FULL, q[0][0], 0);
+}
+
+// Forward, one warp per vector of length 5 <= n <= 32 V CH.  yr may be null
+// (norm only).  The whole warp must call it with the same arguments.
+template <typename T, int V, int CH>
+__device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
+                                             const VecOut<T>& out, int64_t vec) {
+  T v[CH][V];
+  bool nz = false;
+  T m = T(0);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k0 = 32 * V * c + V * lane;
+    if (k0 < n) {
+      Vec<T, V>::load(xr + k0, v[c]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[c][e] = T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      if (k0 + e < n) {
+        nz |= !(v[c][e] == T(0));
+        m = FP<T>::fmax(m, FP<T>::abs(v[c][e]));
+      }
+    }
+  }
+  m = warp_fmax(m);
+  nz = __any_sync(FULL, nz);
+  if (!nz) {  // every component compares equal to zero
+    if (yr) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int k0 = 32 * V * c + V * lane;
+        T z[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) z[e] = T(0);
+        if (k0 < n) Vec<T, V>::store(yr + k0, z);
+      }
+    }
+    if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
+    return;
+  }
+  const int code = select_code<T, true>(m);
+  const T cf = factor_of<T, true>(code);
+  T q[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      v[c][e] = scale_by(code, cf, v[c][e]);
+      q[c][e] = FP<T>::mul(v[c][e], v[c][e]);
+    }
+  }
+  const T rt = FP<T>::sqrt(warp_cr_tree<T, V, CH>(q, n, lane));
+  const T h = FP<T>::rcp(rt);
+  if (yr) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k0 = 32 * V * c + V * lane;
+      if (k0 < n) {
+        T o[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) o[e] = FP<T>::mul(h, v[c][e]);
+        Vec<T, V>::store(yr + k0, o);
+      }
+    }
+  }
+  if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Backward, one warp per vector: dot = CR(y_k g_k), grad_k = ((g_k - y_k dot) h) c.
+template <typename T, int V, int CH>
+__device__ __forceinline__ void warp_backward(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
+                                              int lane, T h, int code) {
+  if (code == CODE_ZERO) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k0 = 32 * V * c + V * lane;
+      T z[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e) z[e] = T(0);
+      if (k0 < n) Vec<T, V>::store(gradr + k0, z);
+    }
+    return;
+  }
+  const T cf = factor_of<T, true>(code);
+  T yv[CH][V], gv[CH][V], q[CH][V];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k0 = 32 * V * c + V * lane;
+    if (k0 < n) {
+      Vec<T, V>::load(yr + k0, yv[c]);
+      Vec<T, V>::load(gr + k0, gv[c]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) { yv[c][e] = T(0); gv[c][e] = T(0); }
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) q[c][e] = FP<T>::mul(yv[c][e], gv[c][e]);
+  }
+  const T dot = warp_cr_tree<T, V, CH>(q, n, lane);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k0 = 32 * V * c + V * lane;
+    if (k0 < n) {
+      T o[V];
+#pragma unroll
+      for (int e = 0; e < V; ++e)
+        o[e] = FP<T>::mul(FP<T>::mul(FP<T>::sub(gv[c][e], FP<T>::mul(yv[c][e], dot)), h), cf);
+      Vec<T, V>::store(gradr + k0, o);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Block layout (B threads, B a power of two in [64, 1024]).  Thread t holds
+// the elements k = B c + t.  Slot j = k mod 1024 belongs to thread j mod B,
+// as its accumulator j / B (G = 1024 / B of them): strides >= B are
+// in-thread, the remaining strides B/2 .. 1 run in warp 0 after one pass
+// through shared memory (lane l takes slots l + 32 i: strides B/2 .. 32
+// in-lane, then shuffles 16 .. 1).
+template <typename T, int B>
+struct BlockShared {
+  T slot[B];
+  T red[B / 32];
+  T total;
+  int item;
+  int flag;
+};
+
+template <typename T, int B>
+__device__ __forceinline__ T block_fmax(T m, BlockShared<T, B>& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  m = warp_fmax(m);
+  if (lane == 0) sh.red[w] = m;
+  __syncthreads();
+  if (w == 0) {
+    T a = lane < B / 32 ? sh.red[lane] : T(0);
+    a = warp_fmax(a);
+    if (lane == 0) sh.total = a;
+  }
+  __syncthreads();
+  const T r = sh.total;
+  __syncthreads();
+  return r;
+}
+
+// acc[i] holds slot i B + t of thread t (strides >= B already applied by the
+// caller).  Returns the CR(n) total to every thread.
+template <typename T, int B>
+__device__ __forceinline__ T block_cr_finish(T acc0, int used, BlockShared<T, B>& sh) {
+  const int t = threadIdx.x;
+  sh.slot[t] = acc0;
+  __syncthreads();
+  if (t < 32) {
+    constexpr int Q = B / 32;
+    T a[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) a[i] = sh.slot[t + 32 * i];
+#pragma unroll
+    for (int p = Q / 2; p >= 1; p >>= 1) {
+#pragma unroll
+      for (int i = 0; i < p; ++i)
+        if (32 * (i + p) + t < used) a[i] = FP<T>::add(a[i], a[i + p]);
+    }
+#pragma unroll
+    for (int p = 16; p >= 1; p >>= 1) {
+      const T o = __shfl_xor_sync(FULL, a[0], p);
+      if (t < p && t + p < used) a[0] = FP<T>::add(a[0], o);
+    }
+    if (t == 0) sh.total = a[0];
+  }
+  __syncthreads();
+  const T r = sh.total;
+  __syncthreads();
+  return r;
+}
+
+// In-thread part of the tree: accumulators of chunk c (c < CH) into slot
+// group c mod G, then strides 512 .. B.
+template <typename T, int B, int CH>
+__device__ __forceinline__ T block_cr_tree(T (&q)[CH], int n, BlockShared<T, B>& sh) {
+  constexpr int G = CR_SLOTS / B;
+  constexpr int NS = CH < G ? CH : G;
+  const int t = threadIdx.x;
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+#pragma unroll
+  for (int c = G; c < CH; ++c)
+    if (B * c + t < n) q[c % G] = FP<T>::add(q[c % G], q[c]);
+#pragma unroll
+  for (int p = G / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int i = 0; i < p; ++i)
+      if (i + p < NS && B * (i + p) + t < used) q[i] = FP<T>::add(q[i], q[i + p]);
+  }
+  return block_cr_finish<T, B>(q[0], used, sh);
+}
+
+// Forward, one block per vector held in registers (n <= B CH).
+template <typename T, int B, int CH>
+__device__ __forceinline__ void block_forward(const T* __restrict__ xr, T* yr, int n, const VecOut<T>& out,
+                                              int64_t vec, BlockShared<T, B>& sh) {
+  const int t = threadIdx.x;
+  T v[CH];
+  bool nz = false;
+  T m = T(0);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k = B * c + t;
+    v[c] = k < n ? __ldcs(xr + k) : T(0);
+    if (k < n) {
+      nz |= !(v[c] == T(0));
+      m = FP<T>::fmax(m, FP<T>::abs(v[c]));
+    }
+  }
+  nz = __syncthreads_or(nz);
+  m = block_fmax<T, B>(m, sh);
+  if (!nz) {
+    if (yr) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (B * c + t < n) __stcs(yr + B * c + t, T(0));
+    }
+    if (t == 0) out.put(vec, T(0), T(0), CODE_ZERO);
+    return;
+  }
+  const int code = select_code<T, true>(m);
+  const T cf = factor_of<T, true>(code);
+  T q[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    v[c] = scale_by(code, cf, v[c]);
+    q[c] = FP<T>::mul(v[c], v[c]);
+  }
+  const T rt = FP<T>::sqrt(block_cr_tree<T, B, CH>(q, n, sh));
+  const T h = FP<T>::rcp(rt);
+  if (yr) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (B * c + t < n) __stcs(yr + B * c + t, FP<T>::mul(h, v[c]));
+  }
+  if (t == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Forward, one block per vector of any length up to 2^20: three passes over
+// the row (largest magnitude, sum of squares, outputs); the second and third
+// usually hit L2.
+template <typename T, int B>
+__device__ __forceinline__ void block_forward_stream(const T* __restrict__ xr, T* yr, int n, const VecOut<T>& out,
+                                                     int64_t vec, BlockShared<T, B>& sh) {
+  constexpr int G = CR_SLOTS / B;
+  const int t = threadIdx.x;
+  bool nz = false;
+  T m = T(0);
+  for (int k = t; k < n; k += B) {
+    const T a = xr[k];
+    nz |= !(a == T(0));
+    m = FP<T>::fmax(m, FP<T>::abs(a));
+  }
+  nz = __syncthreads_or(nz);
+  m = block_fmax<T, B>(m, sh);
+  if (!nz) {
+    if (yr)
+      for (int k = t; k < n; k += B) yr[k] = T(0);
+    if (t == 0) out.put(vec, T(0), T(0), CODE_ZERO);
+    return;
+  }
+  const int code = select_code<T, true>(m);
+  const T cf = factor_of<T, true>(code);
+  T acc[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    const int k = B * i + t;
+    const T a = k < n ? scale_by(code, cf, xr[k]) : T(0);
+    acc[i] = FP<T>::mul(a, a);
+  }
+  for (int base = CR_SLOTS; base < n; base += CR_SLOTS) {
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = base + B * i + t;
+      if (k < n) {
+        const T a = scale_by(code, cf, xr[k]);
+        acc[i] = FP<T>::add(acc[i], FP<T>::mul(a, a));
+      }
+    }
+  }
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+#pragma unroll
+  for (int p = G / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int i = 0; i < p; ++i)
+      if (B * (i + p) + t < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
+  }
+  const T rt = FP<T>::sqrt(block_cr_finish<T, B>(acc[0], used, sh));
+  const T h = FP<T>::rcp(rt);
+  if (yr)
+    for (int k = t; k < n; k += B) yr[k] = FP<T>::mul(h, scale_by(code, cf, xr[k]));
+  if (t == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Backward, one block per vector held in registers (n <= B CH).
+template <typename T, int B, int CH>
+__device__ __forceinline__ void block_backward(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
+                                               T h, int code, BlockShared<T, B>& sh) {
+  const int t = threadIdx.x;
+  if (code == CODE_ZERO) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c)
+      if (B * c + t < n) __stcs(gradr + B * c + t, T(0));
+    return;
+  }
+  const T cf = factor_of<T, true>(code);
+  T yv[CH], gv[CH], q[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k = B * c + t;
+    yv[c] = k < n ? __ldcs(yr + k) : T(0);
+    gv[c] = k < n ? __ldcs(gr + k) : T(0);
+    q[c] = FP<T>::mul(yv[c], gv[c]);
+  }
+  const T dot = block_cr_tree<T, B, CH>(q, n, sh);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k = B * c + t;
+    if (k < n) __stcs(gradr + k, FP<T>::mul(FP<T>::mul(FP<T>::sub(gv[c], FP<T>::mul(yv[c], dot)), h), cf));
+  }
+}
+
+// Backward, one block per vector of any length (two passes over y and g).
+template <typename T, int B>
+__device__ __forceinline__ void block_backward_stream(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr,
+                                                      int n, T h, int code, BlockShared<T, B>& sh) {
+  constexpr int G = CR_SLOTS / B;
+  const int t = threadIdx.x;
+  if (code == CODE_ZERO) {
+    for (int k = t; k < n; k += B) gradr[k] = T(0);
+    return;
+  }
+  const T cf = factor_of<T, true>(code);
+  T acc[G];
+#pragma unroll
+  for (int i = 0; i < G; ++i) {
+    const int k = B * i + t;
+    acc[i] = k < n ? FP<T>::mul(yr[k], gr[k]) : T(0);
+  }
+  for (int base = CR_SLOTS; base < n; base += CR_SLOTS) {
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const int k = base + B * i + t;
+      if (k < n) acc[i] = FP<T>::add(acc[i], FP<T>::mul(yr[k], gr[k]));
+    }
+  }
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+#pragma unroll
+  for (int p = G / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int i = 0; i < p; ++i)
+      if (B * (i + p) + t < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
+  }
+  const T dot = block_cr_finish<T, B>(acc[0], used, sh);
+  for (int k = t; k < n; k += B)
+    gradr[k] = FP<T>::mul(FP<T>::mul(FP<T>::sub(gr[k], FP<T>::mul(yr[k], dot)), h), cf);
+}
+
+}  // namespace ngb

@@ -31,8 +31,8 @@ _TINY = 2.0 ** -1074
 def edge_vectors_d3_f64() -> np.ndarray:
     p = 2.0 ** 1000
     q = 2.0 ** -1060
-    below_tau_min = float(np.nextafter(2.0 ** -482, 0.0))
-    above_tau_max = float(np.nextafter(2.0 ** 510, np.inf))
+    just_below_2m482 = float(np.nextafter(2.0 ** -482, 0.0))
+    just_above_2p510 = float(np.nextafter(2.0 ** 510, np.inf))
     rows = [
         (0.0, 0.0, 0.0), (-0.0, 0.0, 0.0), (0.0, -0.0, -0.0), (-0.0, -0.0, -0.0),
         (1.0, 0.0, 0.0), (0.0, 49.0, 0.0), (0.0, 0.0, -3.0), (1.5 * p, 0.0, 0.0),
@@ -47,8 +47,8 @@ def edge_vectors_d3_f64() -> np.ndarray:
         (_OMEGA, 0.0, 0.0), (_OMEGA, _OMEGA, _OMEGA), (-_OMEGA, _OMEGA, -_OMEGA),
         (2.0 ** 1022, 2.0 ** 1022, 2.0 ** 1022), (1.5 * 2.0 ** 1023, _TINY, 0.0),
         (2.0 ** 511, 2.0 ** 511, 2.0 ** 511),
-        (2.0 ** 510, 0.0, 0.0), (above_tau_max, 1.0, 1.0), (2.0 ** -482, 0.0, 0.0),
-        (below_tau_min, 0.0, 0.0), (2.0 ** -482, 2.0 ** -482, 2.0 ** -482), (2.0 ** -483, 1e-300, 0.0),
+        (2.0 ** 510, 0.0, 0.0), (just_above_2p510, 1.0, 1.0), (2.0 ** -482, 0.0, 0.0),
+        (just_below_2m482, 0.0, 0.0), (2.0 ** -482, 2.0 ** -482, 2.0 ** -482), (2.0 ** -483, 1e-300, 0.0),
         (p, q, 1.0), (q, p, -_TINY), (1.0, 2.0 ** -600, 2.0 ** -600), (2.0 ** -1000, q, _TINY),
         (_TINY, _TINY, _TINY), (_TINY, 0.0, -_TINY), (1e-320, 1e-320, 1e-320), (1.0, 1e-200, 1e-200),
         (1.0, 1.0, 1.0), (1.0, 1e-8, 0.0), (0.6, 0.8, 0.0), (1.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0),

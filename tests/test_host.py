@@ -1,0 +1,177 @@
+"""Host-side checks that need no GPU: the C ABI library builds, loads and
+exports every entry point of include/normgb.h; argument errors are reported
+before any CUDA work; the product code never touches the oracle; the header
+is plain C; the multi-rank sharding logic partitions a batch (gloo,
+world_size 2, each rank running the oracle on its shard)."""
+import ctypes
+import os
+import re
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "normgb.h")
+PKG = os.path.join(ROOT, "paper_1606_06508_gb300")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([A-Za-z_]\w*)\s*\(", text, flags=re.M)
+    return sorted(set(n for n in names if n not in ("defined",)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1606_06508_gb300 import build
+    build.build()
+    from paper_1606_06508_gb300 import _lib
+    return _lib
+
+
+def test_header_is_plain_c():
+    for lang, std in (("c", "c99"), ("c++", "c++11")):
+        r = subprocess.run(["gcc", "-fsyntax-only", "-Wall", "-Werror", "-x", lang, f"-std={std}", HEADER],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert "normalize_f32" in names and "normalize_backward_f64" in names and "ngb_plan_create" in names
+    raw = ctypes.CDLL(lib.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+    assert set(names) <= set(lib.PROTOTYPES), set(names) - set(lib.PROTOTYPES)
+
+
+def test_argument_errors_before_any_cuda_work(lib):
+    L = lib
+    f32 = L.normalize_f32
+    assert f32(None, None, None, None, None, -1, 4, None, None, 0, None) == L.NGB_ERR_INVALID_ARG
+    assert f32(1, 1, None, None, None, 4, -2, None, None, 0, None) == L.NGB_ERR_INVALID_ARG
+    assert f32(1, 1, None, None, None, 4, (1 << 20) + 1, None, None, 0, None) == L.NGB_ERR_UNSUPPORTED
+    assert f32(1, 1, None, None, None, 4, 4, None, None, 0x80, None) == L.NGB_ERR_INVALID_ARG
+    assert f32(1, 1, None, None, None, 4, 4, 8, None, 0, None) == L.NGB_ERR_INVALID_ARG  # offsets with dim > 0
+    assert f32(1, 1, None, None, None, 4, 0, None, None, 0, None) == L.NGB_ERR_INVALID_ARG  # ragged, no offsets
+    assert f32(1, 1, None, None, None, 4, 0, 8, None, 0, None) == L.NGB_ERR_NO_PLAN
+    assert "plan" in L.last_error()
+    assert f32(None, None, None, None, None, 0, 4, None, None, 0, None) == L.NGB_OK  # count 0: no-op
+    assert f32(None, 1, None, None, None, 3, 4, None, None, 0, None) == L.NGB_ERR_INVALID_ARG  # x NULL
+    b = L.normalize_backward_f64
+    assert b(1, 1, 1, None, 1, 3, 4, None, None, 0, None) == L.NGB_ERR_INVALID_ARG  # saved_code NULL
+    assert L.ngb_plan_create(10, 2, 0)[0] == L.NGB_ERR_UNSUPPORTED
+    assert L.ngb_plan_create(-1, 4, 0)[0] == L.NGB_ERR_INVALID_ARG
+    assert L.ngb_plan_create(1 << 31, 4, 0)[0] == L.NGB_ERR_UNSUPPORTED
+    assert L.naive_normalize_f32(1, 1, 5, 7, None) == L.NGB_ERR_INVALID_ARG
+    assert L.ngb_copy(1, 1, -5, None) == L.NGB_ERR_INVALID_ARG
+    assert L.normalize_to_rotation_f32(None, None, None, -1, None) == L.NGB_ERR_INVALID_ARG
+
+
+def test_no_gpu_reports_cuda_error_not_crash(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, p = lib.ngb_plan_create(10, 4, 0)
+    assert st == lib.NGB_ERR_CUDA and p is None and lib.last_error()
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    code = ("import paper_1606_06508_gb300._lib as L; L.LIB_PATH = '/nonexistent/libnormgb.so'; "
+            "import sys\ntry:\n    L.lib()\nexcept ImportError as e:\n    print('IMPORTERROR', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert "IMPORTERROR" in r.stdout, r.stdout + r.stderr
+
+
+def test_package_import_is_lazy():
+    code = ("import sys, paper_1606_06508_gb300, paper_1606_06508_gb300.synth; "
+            "print('LOADED' if 'paper_1606_06508_gb300._lib' in sys.modules and "
+            "sys.modules['paper_1606_06508_gb300._lib']._lib is not None else 'LAZY')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert "LAZY" in r.stdout, r.stdout + r.stderr
+
+
+def test_product_never_touches_the_oracle():
+    """The library, its binding and the input generators share nothing with
+    oracle/, and the oracle includes nothing of the library."""
+    for dirpath, _, files in os.walk(PKG):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert not re.search(r"\b(import|from)\s+oracle\b|\boracle\.\w|#include[^\n]*oracle", text), \
+                    f"{fn} uses the oracle"
+    for fn in ("normalize_oracle.c", "oracle_impl.h", "__init__.py"):
+        text = open(os.path.join(ROOT, "oracle", fn)).read()
+        assert "csrc" not in text and "normgb" not in text and "paper_1606_06508_gb300" not in text, fn
+
+
+def test_synth_holds_no_method_arithmetic():
+    text = open(os.path.join(PKG, "synth.py")).read()
+    for word in ("sqrt", "tau_", "sigma", "rcp", "normalize("):
+        assert word not in text, word
+
+
+# ----------------------------------------------------------------------------- sharding
+def test_shard_ranges_partition():
+    from paper_1606_06508_gb300 import shard, synth
+    for count in (0, 1, 7, 1000):
+        for world in (1, 2, 3, 8):
+            rs = [shard.dense_range(count, world, r) for r in range(world)]
+            assert rs[0][0] == 0 and rs[-1][1] == count
+            assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+    lengths = synth.ragged_lengths(20000, seed=3)
+    off = synth.offsets_from_lengths(lengths)
+    for world in (2, 4, 8):
+        rs = [shard.ragged_range(off, world, r) for r in range(world)]
+        assert rs[0][0] == 0 and rs[-1][1] == len(lengths)
+        assert all(rs[i][1] == rs[i + 1][0] for i in range(world - 1))
+        elems = [off[b] - off[a] for a, b in rs]
+        assert max(elems) - min(elems) <= 2 * 4096 + off[-1] // 100
+
+
+def _gloo_worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    sys.path.insert(0, ROOT)
+    import oracle
+    from paper_1606_06508_gb300 import shard, synth
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    lengths = synth.ragged_lengths(3000, seed=3, nmax=600)
+    off = synth.offsets_from_lengths(lengths)
+    x = synth.ragged_values(lengths, np.float64, seed=3)
+    a, b = shard.ragged_range(off, world, rank)
+    sub_off = off[a:b + 1] - off[a]
+    y = oracle.normalize(x[off[a]:off[b]], dim=0, offsets=sub_off)[0]
+    parts = [None] * world
+    dist.all_gather_object(parts, (a, b, y))
+    if rank == 0:
+        full = np.concatenate([p[2] for p in sorted(parts, key=lambda t: t[0])])
+        ref = oracle.normalize(x, dim=0, offsets=off)[0]
+        q.put(bool(np.array_equal(full, ref)) and parts[0][1] == parts[1][0])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_two_ranks_shard_and_gather():
+    import torch.multiprocessing as mp
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_gloo_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert all(p.exitcode == 0 for p in procs)
+    assert q.get(timeout=5) is True
