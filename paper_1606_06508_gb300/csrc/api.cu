@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/normgb.h"
+#include "normgb.h"
 #include "ngb_internal.h"
 
 namespace {

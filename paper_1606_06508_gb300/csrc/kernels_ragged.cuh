@@ -8,10 +8,13 @@
 //    (n > warp_max), the warp list (thread_max < n <= warp_max) and the thread
 //    list (n <= thread_max).  Appends are aggregated per block: one atomic per
 //    block and list.
-// 2. k_ragged_fwd / k_ragged_bwd run one wave of persistent blocks that take
-//    work from the three lists in that order (longest vectors first) through
+// 2. Forward: k_ragged runs one wave of persistent blocks that take work
+//    from the three lists in that order (longest vectors first) through
 //    atomic tickets, whole blocks on block items, warps on batches of warp
 //    items, lanes on thread items.  No block ever waits for another.
+// 3. Backward: one plain grid-stride kernel per list (k_ragged_bwd_blocks,
+//    k_ragged_bwd_warps, k_ragged_bwd_threads), each shaped like the dense
+//    backward kernels.
 // Every mapping evaluates the same operations in the same order (the paper's
 // Algorithms 3-7 for n <= 4, the order CR(n) for n >= 5), so the results do
 // not depend on the mapping, the grid or the order in which items are taken.
@@ -163,8 +166,9 @@ struct RaggedArgs {
   int64_t count;
 };
 
-// WCH: chunks of 32 per lane for warp items (warp_max <= 32 WCH).
-template <typename T, int B, int WCH, bool BWD>
+// Forward persistent kernel.  WCH: chunks of 32 per lane for warp items
+// (warp_max <= 32 WCH).
+template <typename T, int B, int WCH>
 __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
   const int t = threadIdx.x, lane = t & 31;
@@ -183,18 +187,10 @@ __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
     const int64_t vec = Lb[it];
     const int64_t s = a.off[vec];
     const int n = (int)(a.off[vec + 1] - s);
-    if constexpr (!BWD) {
-      T* yr = a.y ? a.y + s : nullptr;
-      if (n <= 8 * B) block_forward<T, B, 8>(a.x + s, yr, n, a.out, vec, sh);
-      else if (n <= 16 * B) block_forward<T, B, 16>(a.x + s, yr, n, a.out, vec, sh);
-      else block_forward_stream<T, B>(a.x + s, yr, n, a.out, vec, sh);
-    } else {
-      const T h = a.h_in[vec];
-      const int code = a.c_in[vec];
-      if (n <= 8 * B) block_backward<T, B, 8>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
-      else if (n <= 16 * B) block_backward<T, B, 16>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
-      else block_backward_stream<T, B>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
-    }
+    T* yr = a.y ? a.y + s : nullptr;
+    if (n <= 8 * B) block_forward<T, B, 8>(a.x + s, yr, n, a.out, vec, sh);
+    else if (n <= 16 * B) block_forward<T, B, 16>(a.x + s, yr, n, a.out, vec, sh);
+    else block_forward_stream<T, B>(a.x + s, yr, n, a.out, vec, sh);
   }
 
   // warp items, WARP_BATCH per ticket
@@ -207,11 +203,7 @@ __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
       const int64_t vec = Lw[base + j];
       const int64_t s = a.off[vec];
       const int n = (int)(a.off[vec + 1] - s);
-      if constexpr (!BWD) {
-        warp_item_fwd<T, WCH>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
-      } else {
-        warp_item_bwd<T, WCH>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
-      }
+      warp_item_fwd<T, WCH>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
     }
   }
 
@@ -228,42 +220,111 @@ __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
         const int64_t vec = Lt[it];
         const int64_t s = a.off[vec];
         const int n = (int)(a.off[vec + 1] - s);
-        if constexpr (!BWD) {
-          thread_item_fwd<T>(a.x + s, a.y ? a.y + s : nullptr, n, a.out, vec);
-        } else {
-          thread_item_bwd<T>(a.x + s, a.g + s, a.y + s, n, a.h_in[vec], a.c_in[vec]);
-        }
+        thread_item_fwd<T>(a.x + s, a.y ? a.y + s : nullptr, n, a.out, vec);
       }
     }
   }
 }
 
+// Backward, block list: one block per vector, grid-stride over the list.
+template <typename T, int B>
+__global__ void __launch_bounds__(B) k_ragged_bwd_blocks(RaggedArgs<T> a) {
+  __shared__ BlockShared<T, B> sh;
+  const int nblk = a.sc.counts[0];
+  const int32_t* Lb = a.sc.items;
+  for (int it = blockIdx.x; it < nblk; it += gridDim.x) {
+    const int64_t vec = Lb[it];
+    const int64_t s = a.off[vec];
+    const int n = (int)(a.off[vec + 1] - s);
+    const T h = a.h_in[vec];
+    const int code = a.c_in[vec];
+    if (n <= 8 * B) block_backward<T, B, 8>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+    else if (n <= 16 * B) block_backward<T, B, 16>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+    else block_backward_stream<T, B>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+  }
+}
+
+// Backward, warp list: one warp per vector, warp-stride over the list.
+template <typename T, int WCH>
+__global__ void __launch_bounds__(256) k_ragged_bwd_warps(RaggedArgs<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int nwarp = a.sc.counts[1];
+  const int32_t* Lw = a.sc.items + a.count;
+  const int w0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+  for (int it = w0; it < nwarp; it += nw) {
+    const int64_t vec = Lw[it];
+    const int64_t s = a.off[vec];
+    const int n = (int)(a.off[vec + 1] - s);
+    warp_item_bwd<T, WCH>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
+  }
+}
+
+// Backward, thread list: one thread per vector, grid-stride over the list.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ragged_bwd_threads(RaggedArgs<T> a) {
+  const int nthr = a.sc.counts[2];
+  const int32_t* Lt = a.sc.items + 2 * a.count;
+  const int stride = (int)((int64_t)gridDim.x * blockDim.x);
+  for (int it = (int)((int64_t)blockIdx.x * blockDim.x + threadIdx.x); it < nthr; it += stride) {
+    const int64_t vec = Lt[it];
+    const int64_t s = a.off[vec];
+    const int n = (int)(a.off[vec + 1] - s);
+    thread_item_bwd<T>(a.x + s, a.g + s, a.y + s, n, a.h_in[vec], a.c_in[vec]);
+  }
+}
+
 // ---------------------------------------------------------------------------
-template <typename T, int B, int WCH, bool BWD>
+template <typename T, int B, int WCH>
 inline int full_wave_of() {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ragged<T, B, WCH, BWD>, B, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ragged<T, B, WCH>, B, 0);
   if (per_sm < 1) per_sm = 1;
   return per_sm * device_sm_count();
 }
 
-template <typename T, bool BWD>
+template <typename T>
 inline int full_wave_dispatch(const RaggedMapping& m) {
   const bool big = m.warp_max > 512;
-  if (m.block_threads == 512) return big ? full_wave_of<T, 512, 32, BWD>() : full_wave_of<T, 512, 16, BWD>();
-  return big ? full_wave_of<T, 256, 32, BWD>() : full_wave_of<T, 256, 16, BWD>();
+  if (m.block_threads == 512) return big ? full_wave_of<T, 512, 32>() : full_wave_of<T, 512, 16>();
+  return big ? full_wave_of<T, 256, 32>() : full_wave_of<T, 256, 16>();
 }
 
-template <typename T, bool BWD>
+template <typename K>
+inline int wave_of(K kernel, int threads) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  return per_sm * device_sm_count();
+}
+
+template <typename T>
+inline void launch_backward_lists(const RaggedArgs<T>& a, const RaggedMapping& m, cudaStream_t s) {
+  const int cap = m.grid_blocks > 0 ? m.grid_blocks : 1 << 30;
+  auto clamp = [cap](int g) { return g < cap ? g : cap; };
+  if (m.block_threads == 512) {
+    k_ragged_bwd_blocks<T, 512><<<clamp(wave_of(k_ragged_bwd_blocks<T, 512>, 512)), 512, 0, s>>>(a);
+  } else {
+    k_ragged_bwd_blocks<T, 256><<<clamp(wave_of(k_ragged_bwd_blocks<T, 256>, 256)), 256, 0, s>>>(a);
+  }
+  if (m.warp_max > 512) {
+    k_ragged_bwd_warps<T, 32><<<clamp(wave_of(k_ragged_bwd_warps<T, 32>, 256)), 256, 0, s>>>(a);
+  } else {
+    k_ragged_bwd_warps<T, 16><<<clamp(wave_of(k_ragged_bwd_warps<T, 16>, 256)), 256, 0, s>>>(a);
+  }
+  k_ragged_bwd_threads<T><<<clamp(wave_of(k_ragged_bwd_threads<T>, 256)), 256, 0, s>>>(a);
+}
+
+template <typename T>
 inline void launch_persistent(const RaggedArgs<T>& a, const RaggedMapping& m, cudaStream_t s) {
-  const int grid = m.grid_blocks > 0 ? m.grid_blocks : full_wave_dispatch<T, BWD>(m);
+  const int grid = m.grid_blocks > 0 ? m.grid_blocks : full_wave_dispatch<T>(m);
   const bool big = m.warp_max > 512;
   if (m.block_threads == 512) {
-    if (big) k_ragged<T, 512, 32, BWD><<<grid, 512, 0, s>>>(a);
-    else k_ragged<T, 512, 16, BWD><<<grid, 512, 0, s>>>(a);
+    if (big) k_ragged<T, 512, 32><<<grid, 512, 0, s>>>(a);
+    else k_ragged<T, 512, 16><<<grid, 512, 0, s>>>(a);
   } else {
-    if (big) k_ragged<T, 256, 32, BWD><<<grid, 256, 0, s>>>(a);
-    else k_ragged<T, 256, 16, BWD><<<grid, 256, 0, s>>>(a);
+    if (big) k_ragged<T, 256, 32><<<grid, 256, 0, s>>>(a);
+    else k_ragged<T, 256, 16><<<grid, 256, 0, s>>>(a);
   }
 }
 
@@ -291,11 +352,11 @@ cudaError_t launch_ragged_impl(const T* x, T* y, T* norm, T* saved_h, int8_t* sa
   if (!backward) {
     a.x = x; a.y = y; a.g = nullptr; a.h_in = nullptr; a.c_in = nullptr;
     a.out = VecOut<T>{norm, saved_h, saved_code};
-    launch_persistent<T, false>(a, map, s);
+    launch_persistent<T>(a, map, s);
   } else {
     a.x = x; a.y = grad; a.g = g; a.h_in = h_in; a.c_in = code_in;
     a.out = VecOut<T>{nullptr, nullptr, nullptr};
-    launch_persistent<T, true>(a, map, s);
+    launch_backward_lists<T>(a, map, s);
   }
   return cudaGetLastError();
 }

@@ -12,6 +12,7 @@ cudaError_t launch_ragged<float>(const float* x, float* y, float* norm, float* s
 }
 template <>
 int ragged_full_wave<float>(const RaggedMapping& map, bool backward) {
-  return backward ? full_wave_dispatch<float, true>(map) : full_wave_dispatch<float, false>(map);
+  // the backward lists run one full wave per kernel
+  return backward ? 0 : full_wave_dispatch<float>(map);
 }
 }  // namespace ngb

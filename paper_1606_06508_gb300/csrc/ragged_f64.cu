@@ -12,6 +12,7 @@ cudaError_t launch_ragged<double>(const double* x, double* y, double* norm, doub
 }
 template <>
 int ragged_full_wave<double>(const RaggedMapping& map, bool backward) {
-  return backward ? full_wave_dispatch<double, true>(map) : full_wave_dispatch<double, false>(map);
+  // the backward lists run one full wave per kernel
+  return backward ? 0 : full_wave_dispatch<double>(map);
 }
 }  // namespace ngb

@@ -422,3 +422,37 @@ def test_backward_zero_vector(oracle_lib):
         y, r, h, c = oracle_lib.normalize(x, dim=n, flags=flags)
         grad = oracle_lib.backward(y, np.ones(n), h, c, dim=n)
         assert np.all(grad == 0) and not np.any(np.signbit(grad))
+
+
+# ---------------------------------------------------------------- rotation matrix (Section 4)
+@pytest.mark.parametrize("f", ["f32", "f64"])
+def test_rotation_against_exact_matrix(oracle_lib, f):
+    """R(q^) against the exact R(q) = (general matrix) / |q|^2 in rational
+    arithmetic.  Lemma 2 bounds |q^_i q^_j - q_i q_j / r^2| by
+    (1.001 + 8.001 |q_i q_j| / r^2) u; each entry adds at most three more
+    roundings of values <= 2, so every entry is within 30 u."""
+    fmt = F32 if f == "f32" else F64
+    dt = DT[f]
+    q = synth.quaternions_f32(1500, seed=12).astype(dt) if f == "f32" else synth.vectors_f64(1500, 4, seed=12)
+    R, r = oracle_lib.rotation(q)
+    u = fmt.u
+    for i in range(q.shape[0]):
+        a, b, c, d = (fr(v) for v in q[i])
+        s = a * a + b * b + c * c + d * d
+        if s == 0:
+            continue
+        ex = [[a * a + d * d - b * b - c * c, 2 * (a * b - c * d), 2 * (a * c + b * d)],
+              [2 * (a * b + c * d), b * b + d * d - a * a - c * c, 2 * (b * c - a * d)],
+              [2 * (a * c - b * d), 2 * (b * c + a * d), c * c + d * d - a * a - b * b]]
+        for j in range(3):
+            for k in range(3):
+                assert abs(fr(R[i, j, k]) - ex[j][k] / s) <= 30 * u, (i, j, k)
+
+
+def test_rotation_special_cases(oracle_lib):
+    R, r = oracle_lib.rotation(np.zeros((1, 4)))
+    assert R[0].tolist() == [[-1, 0, 0], [0, -1, 0], [0, 0, 1]] and r[0] == 0  # q^ = (0, 0, 1, 0)
+    R, _ = oracle_lib.rotation(np.array([[0.0, 0.0, 0.0, 5.0]]))
+    assert R[0].tolist() == [[1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    R, _ = oracle_lib.rotation(np.array([[2.0 ** -1000, 0.0, 0.0, 0.0]]))  # tiny: scaled; half turn about axis 1
+    assert R[0].tolist() == [[1, 0, 0], [0, -1, 0], [0, 0, -1]]
