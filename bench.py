@@ -1,6 +1,6 @@
 """Benchmark of batched accurate normalization (arXiv 1606.06508) on GB300.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras] [--count C]
 
 One step = one call of the library on the whole per-GPU workload: 2^26
 binary32 quaternions (1 GiB in, 1 GiB out), normalized with the scaling
@@ -212,7 +212,7 @@ def cpu_baseline_quat():
         oracle.normalize_threads(x.reshape(-1), dim=4, threads=threads)
         reps += 1
         dt = time.perf_counter() - t0
-        if dt > 10.0 or reps >= 400:
+        if dt > 10.0 or reps >= 4000:
             break
     return {"value": reps * sample / dt, "unit": "vectors/s", "cores": threads, "kind": "oracle",
             "sample": f"{reps} x {sample} quaternions of the same recipe ({dt:.1f} s), oracle on {threads} host "
@@ -225,7 +225,8 @@ def parity_sample(x, y, api_mod):
     import oracle
     n = x.shape[0]
     rng = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([np.arange(1024), rng.choice(n, 1 << 16, replace=False), np.arange(n - 1024, n)]))
+    idx = np.unique(np.concatenate([np.arange(min(n, 1024)), rng.choice(n, min(n, 1 << 16), replace=False),
+                                    np.arange(max(0, n - 1024), n)]))
     it = torch.from_numpy(idx).to(x.device)
     xs = x[it].cpu().numpy()
     ys = y[it].cpu().numpy().reshape(-1)
@@ -331,12 +332,13 @@ def run_ours(args):
 
     peak, peak_src = peaks()
     s = torch.cuda.current_stream()
-    x = synth.quaternions_f32_torch(QUAT_COUNT, seed=1 + 1000 * rank, device=dev)
+    count = args.count
+    x = synth.quaternions_f32_torch(count, seed=1 + 1000 * rank, device=dev)
     y = torch.empty_like(x)
     xp, yp = x.data_ptr(), y.data_ptr()
 
     def step():
-        st = L.normalize_f32(xp, yp, None, None, None, QUAT_COUNT, 4, None, None, 0, s.cuda_stream)
+        st = L.normalize_f32(xp, yp, None, None, None, count, 4, None, None, 0, s.cuda_stream)
         if st:
             L.check(st, "normalize_f32")
 
@@ -375,24 +377,25 @@ def run_ours(args):
     result = None
     if rank == 0:
         secs = ms * 1e-3
-        value = world * args.steps * QUAT_COUNT / secs
+        value = world * args.steps * count / secs
         launch_s = statistics.mean(per_launch) * 1e-3
-        achieved = QUAT_COUNT * QUAT_BYTES / launch_s / 1e9
+        achieved = count * QUAT_BYTES / launch_s / 1e9
         traffic, tnote = traffic_for(KERNEL)
         result = {
             "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "vectors_per_gpu": QUAT_COUNT,
-                       "algorithmic_bytes_per_step_per_gpu": QUAT_COUNT * QUAT_BYTES,
+            "config": {"workload": WORKLOAD if count == QUAT_COUNT else f"{count} quaternions (profiling size)",
+                       "vectors_per_gpu": count,
+                       "algorithmic_bytes_per_step_per_gpu": count * QUAT_BYTES,
                        "l2": "inputs larger than L2 (1 GiB in, 1 GiB out per GPU); no flush",
                        "parallelism": f"independent batch per GPU x{world}"},
-            "GB_per_s": world * args.steps * QUAT_COUNT * QUAT_BYTES / secs / 1e9,
+            "GB_per_s": world * args.steps * count * QUAT_BYTES / secs / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "kernel": KERNEL,
                          "peak_source": peak_src + ("; of measured" if peak_src.startswith("measured") else
                                                     "; of fallback"),
-                         "achieved_note": "32 B algorithmic per quaternion x 2^26 / mean event time of "
+                         "achieved_note": f"32 B algorithmic per quaternion x {count} / mean event time of "
                                           f"{len(per_launch)} single-launch steps",
                          "traffic_note": tnote},
             "gpu_launches": args.steps,
@@ -425,8 +428,8 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ems = float(t.item())
     if rank == 0:
-        result["e2e"] = {"value": world * e2e_steps * QUAT_COUNT / (ems * 1e-3), "unit": "vectors/s",
-                         "h2d_bytes_per_step": QUAT_COUNT * 16, "d2h_bytes_per_step": QUAT_COUNT * 16,
+        result["e2e"] = {"value": world * e2e_steps * count / (ems * 1e-3), "unit": "vectors/s",
+                         "h2d_bytes_per_step": count * 16, "d2h_bytes_per_step": count * 16,
                          "steps": e2e_steps, "note": "pinned host x -> device, normalize_f32, device y -> pinned host"}
         result["parity"] = parity_sample(x, y, api)
         if world == 1:
@@ -448,6 +451,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--count", type=int, default=QUAT_COUNT,
+                    help="quaternions per GPU (default 2^26, the headline workload; smaller only for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
