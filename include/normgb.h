@@ -174,6 +174,37 @@ ngb_status ngb_copy(void* dst, const void* src, int64_t bytes, ngb_stream_t stre
 ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream);
 ngb_status naive_normalize_f64(const double* x, double* y, int64_t count, int32_t dim, ngb_stream_t stream);
 
+/* Largest batch accepted by normalize_ragged_f32_noalloc. */
+#define NGB_NOALLOC_MAX_COUNT 262144
+
+/*
+ * normalize_ragged_f32_noalloc -- the ragged binary32 forward pass of
+ * normalize_f32 (dim == 0) for callers that must not allocate device memory.
+ * The paper has no counterpart: it is a deployment variant of the library.
+ * Some callers cannot call cudaMalloc: code running under another
+ * framework's memory pool (a direct allocation would bypass the pool or fail
+ * because the pool has already reserved the device memory), latency-bound
+ * loops where an allocation could synchronize the device, and plugins whose
+ * host forbids them to allocate.  They pass inputs and outputs only.
+ *
+ * The work lists that a plan would allocate live instead in one file-scope
+ * device array of (8 + 3 * NGB_NOALLOC_MAX_COUNT) 32-bit words (about 3 MiB),
+ * which every device that loads the library holds until the process exits.
+ * count > NGB_NOALLOC_MAX_COUNT returns NGB_ERR_UNSUPPORTED (no work queued).
+ * The first call on a device looks up the device address of that array (with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array and clears its counters on `stream` before
+ * use, so calls that overlap on the GPU (two streams, or two threads with
+ * different streams) race and must be serialized by the caller.  Vectors
+ * with bad offsets are skipped (there is no plan to report them); results
+ * are bit-identical to normalize_f32 with a plan.  No cudaMalloc, cudaFree
+ * or allocating library routine is called.
+ * x, y, norm, saved_h, saved_code, count, offsets: as normalize_f32 (dim == 0);
+ * flags: NGB_VALIDATE_OFFSETS or 0.
+ */
+ngb_status normalize_ragged_f32_noalloc(const float* x, float* y, float* norm, float* saved_h, int8_t* saved_code,
+                                        int64_t count, const int64_t* offsets, uint32_t flags, ngb_stream_t stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* ngb_last_error(void);
 /* Library version string. */

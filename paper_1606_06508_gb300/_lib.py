@@ -54,6 +54,7 @@ PROTOTYPES = {
     "ngb_copy": (ST, [P, P, I64, P]),
     "naive_normalize_f32": (ST, [P, P, I64, I32, P]),
     "naive_normalize_f64": (ST, [P, P, I64, I32, P]),
+    "normalize_ragged_f32_noalloc": (ST, [P, P, P, P, P, I64, P, U32, P]),
     "ngb_last_error": (ctypes.c_char_p, []),
     "ngb_version": (ctypes.c_char_p, []),
 }
@@ -121,6 +122,8 @@ normalize_to_rotation_f64 = _fwd("normalize_to_rotation_f64")
 ngb_copy = _fwd("ngb_copy")
 naive_normalize_f32 = _fwd("naive_normalize_f32")
 naive_normalize_f64 = _fwd("naive_normalize_f64")
+normalize_ragged_f32_noalloc = _fwd("normalize_ragged_f32_noalloc")
+NGB_NOALLOC_MAX_COUNT = 262144
 
 
 def ngb_plan_create(count: int, dtype_bytes: int, capacity: int = 0):

@@ -25,7 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-fmad=false", "-ftz=false",
            "-prec-div=true", "-prec-sqrt=true", "-I", INCLUDE]
 
-SOURCES = ["api.cu", "fixed_f32.cu", "fixed_f64.cu", "ragged_f32.cu", "ragged_f64.cu", "extras.cu"]
+SOURCES = ["api.cu", "fixed_f32.cu", "fixed_f64.cu", "ragged_f32.cu", "ragged_f64.cu", "extras.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

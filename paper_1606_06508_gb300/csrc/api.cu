@@ -37,6 +37,10 @@ bool stream_capturing(cudaStream_t s) {
 
 }  // namespace
 
+namespace ngb {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ngb
+
 struct GraphKey {
   const void* p[10];
   int64_t count;

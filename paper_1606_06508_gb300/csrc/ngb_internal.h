@@ -4,12 +4,17 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace ngb {
 
 template <typename T> struct VecOut;
 
 // Multiprocessor count of the current device (cached per device).
 int device_sm_count();
+
+// Sets the message returned by ngb_last_error() on this thread.
+void set_last_error(const std::string& msg);
 
 // Dense [count][dim] batches.
 template <typename T>
