@@ -1,23 +1,29 @@
 """Benchmark of batched accurate normalization (arXiv 1606.06508) on GB300.
 
-python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-extras] [--count C]
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload NAME] [--count C] [--no-extras]
 
-One step = one call of the library on the whole per-GPU workload: 2^26
-binary32 quaternions (1 GiB in, 1 GiB out), normalized with the scaling
-algorithm (Algorithm 7) -- the workload the headline metric is quoted on.
-Inputs are resident in HBM when the timed region starts and larger than L2,
-so no flush is needed between steps.  Rank 0 prints one JSON line with the
-whole-job throughput (vectors/s), the roofline of the dominant kernel
-(achieved algorithmic bytes per launch over its event-timed duration, against
-the measured HBM copy bandwidth), the oracle timed on the host cores on a
-bounded sample (cpu_baseline), an end-to-end figure through host buffers
-(e2e), the SM clocks sampled during the timed region, and a parity check of
-sampled outputs against the oracle.  With N > 1 (torchrun) each rank
-normalizes its own batch (weak scaling, no data exchange); the timing is the
-max over ranks.
+Default workload (the headline): one step = one library call on 2^26
+binary32 quaternions (1 GiB in, 1 GiB out) normalized with the scaling
+algorithm (Algorithm 7).  Inputs are resident in HBM when the timed region
+starts and larger than L2, so no flush is needed between steps.  Rank 0 prints
+one JSON line with the whole-job throughput (vectors/s), the roofline of the
+dominant kernel (algorithmic bytes per launch over its event-timed duration,
+against the measured HBM copy bandwidth), the oracle timed on the host cores
+on a bounded sample (cpu_baseline), an end-to-end figure through pinned host
+buffers (e2e), the SM clocks sampled during the timed region, a bitwise parity
+check of sampled outputs against the oracle, and (N = 1, unless --no-extras)
+short secondary measurements of the other workloads.
+
+--workload selects another workload of the method for the same JSON line
+(per-workload evidence and profiling): fwdbwd_quat, rows_f32, rows_f64,
+ragged_f32, ragged_f64, fwdbwd_ragged_f64, vec3_f64.
+
+With N > 1 (torchrun) each rank normalizes its own batch (weak scaling, no
+data exchange); the timing is the max over ranks.
 
 --impl reference times the oracle (plain single-threaded C, run on all host
-cores over contiguous ranges) on bounded samples of the same workload.
+cores over contiguous vector ranges) on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -39,10 +45,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "normalized vectors/s & HBM GB/s (% peak), fwd and fwd+bwd, 0-ulp vs oracle"
 QUAT_COUNT = 1 << 26
-QUAT_BYTES = 32  # 16 B read + 16 B written per quaternion
-WORKLOAD = "2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 wide-exponent/N(0,1) components"
-KERNEL = "k_small_vec16<float,4>"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+L2_BYTES = 126 * 1024 * 1024
 
 
 def peaks():
@@ -64,13 +68,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources (else None)."""
+def traffic_for(workload: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel sources (else None)."""
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d.get(kernel)
+        e = d.get(workload)
         if e and e.get("source_hash") == kernel_source_hash():
             return e["dram_bytes_per_launch"], e.get("note")
     except Exception:
@@ -85,8 +89,8 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int):
-        self.gpu = gpu_index
+    def __init__(self, gpu_id: str):
+        self.gpu = gpu_id
         self.proc = None
         self.lines = []
         self.marks = []
@@ -156,42 +160,12 @@ def cpu_threads():
         return os.cpu_count() or 1
 
 
-# ---------------------------------------------------------------------------- reference arm
-def run_reference(args):
-    world, rank, _ = dist_setup()
-    if rank != 0:
-        return 0
-    import oracle
-    from paper_1606_06508_gb300 import synth
-    oracle.build()
-    threads = cpu_threads()
-    sample = 1 << 17
-    x = synth.quaternions_f32(sample, seed=1)
-    for _ in range(args.warmup):
-        oracle.normalize_threads(x.reshape(-1), dim=4, threads=threads)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.normalize_threads(x.reshape(-1), dim=4, threads=threads)
-    dt = time.perf_counter() - t0
-    v = args.steps * sample / dt
-    line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "reference_step": f"{sample} quaternions of the same recipe (bounded sample)"},
-        "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": threads, "kind": "oracle",
-                         "sample": f"{sample} quaternions per step, oracle on {threads} host threads over contiguous ranges"},
-        "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-    return 0
-
-
-# ---------------------------------------------------------------------------- our arm
-def time_events(fn, iters, stream):
+def time_events(fn, iters, stream, between=None):
     import torch
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(iters)]
     for a, b in evs:
+        if between:
+            between()
         a.record(stream)
         fn()
         b.record(stream)
@@ -199,120 +173,286 @@ def time_events(fn, iters, stream):
     return [a.elapsed_time(b) for a, b in evs]
 
 
-def cpu_baseline_quat():
-    """The oracle on the host cores on a bounded sample of the workload, ~10 s."""
-    import oracle
+# ---------------------------------------------------------------------------- host samples (oracle side)
+def host_sample(name: str, n: int):
+    """A bounded host sample of a workload's recipe: (x, dim, offsets, units)."""
     from paper_1606_06508_gb300 import synth
+    if name in ("quat", "fwdbwd_quat"):
+        x = synth.quaternions_f32(n, seed=101)
+        return x.reshape(-1), 4, None, n
+    if name in ("rows_f32", "rows_f64"):
+        dt = np.float32 if name.endswith("f32") else np.float64
+        rows = max(1, n // 256)
+        return synth.rows(rows, 256, dt, seed=102).reshape(-1), 256, None, rows
+    if name == "vec3_f64":
+        x = synth.vectors3_f64(n, seed=103)
+        return x.reshape(-1), 3, None, x.shape[0]
+    dt = np.float64 if "f64" in name else np.float32
+    kind, nmax = ("loguniform", 1024) if name == "fwdbwd_ragged_f64" else ("mixture", 4096)
+    cnt = max(1, n // 300)
+    lengths = synth.ragged_lengths(cnt, seed=104, kind=kind, nmax=nmax)
+    return synth.ragged_values(lengths, dt, seed=104), 0, synth.offsets_from_lengths(lengths), cnt
+
+
+def cpu_baseline(name: str, seconds: float = 10.0):
+    """The oracle as it stands, on all host cores over contiguous vector ranges,
+    repeated on a bounded sample of the workload for about `seconds`."""
+    import oracle
+    oracle.build()
     threads = cpu_threads()
-    sample = 1 << 22
-    x = synth.quaternions_f32(sample, seed=101)
-    oracle.normalize_threads(x.reshape(-1), dim=4, threads=threads)
+    x, dim, off, units = host_sample(name, 1 << 21)
+    oracle.normalize_threads(x, dim, off, threads=threads)
     reps, t0 = 0, time.perf_counter()
     while True:
-        oracle.normalize_threads(x.reshape(-1), dim=4, threads=threads)
+        oracle.normalize_threads(x, dim, off, threads=threads)
         reps += 1
         dt = time.perf_counter() - t0
-        if dt > 10.0 or reps >= 4000:
+        if dt > seconds or reps >= 100000:
             break
-    return {"value": reps * sample / dt, "unit": "vectors/s", "cores": threads, "kind": "oracle",
-            "sample": f"{reps} x {sample} quaternions of the same recipe ({dt:.1f} s), oracle on {threads} host "
-                      "threads over contiguous vector ranges"}
+    return {"value": reps * units / dt, "unit": "vectors/s", "cores": threads, "kind": "oracle",
+            "sample": f"{reps} x {units} vectors of the same recipe ({dt:.1f} s, forward), oracle on {threads} "
+                      "host threads over contiguous vector ranges"}
 
 
-def parity_sample(x, y, api_mod):
-    """Sampled outputs of the timed workload against the oracle (bitwise)."""
+# ---------------------------------------------------------------------------- parity of the timed outputs
+def _bits_mismatch(a, b):
+    ui = np.uint32 if a.dtype == np.float32 else np.uint64
+    nan = np.isnan(a) & np.isnan(b)
+    return int(np.count_nonzero((a.view(ui) != b.view(ui)) & ~nan))
+
+
+def parity_dense(x, y, dim, k=1 << 14, grad=None, g=None):
     import torch
     import oracle
     n = x.shape[0]
     rng = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([np.arange(min(n, 1024)), rng.choice(n, min(n, 1 << 16), replace=False),
-                                    np.arange(max(0, n - 1024), n)]))
+    idx = np.unique(np.concatenate([np.arange(min(n, 256)), rng.choice(n, min(n, k), replace=False),
+                                    np.arange(max(0, n - 256), n)]))
     it = torch.from_numpy(idx).to(x.device)
-    xs = x[it].cpu().numpy()
-    ys = y[it].cpu().numpy().reshape(-1)
-    oy = oracle.normalize(xs.reshape(-1), dim=4)[0]
-    nan = np.isnan(ys) & np.isnan(oy)
-    bad = int(np.count_nonzero((ys.view(np.uint32) != oy.view(np.uint32)) & ~nan))
+    xs = x[it].cpu().numpy().reshape(-1)
+    oy, _, oh, oc = oracle.normalize(xs, dim=dim)
+    bad = _bits_mismatch(y[it].cpu().numpy().reshape(-1), oy)
+    if grad is not None:
+        og = oracle.backward(oy, g[it].cpu().numpy().reshape(-1), oh, oc, dim=dim)
+        bad += _bits_mismatch(grad[it].cpu().numpy().reshape(-1), og)
     return {"sampled_vectors": int(idx.size), "mismatching_values": bad, "max_ulp_vs_oracle": 0 if bad == 0 else None}
 
 
-def extras(api, synth, torch, peak):
-    """Secondary measurements (each one call repeated, CUDA events): the
-    forward+backward form, rows, ragged, the copy ceiling, the naive algorithm."""
-    out = {}
-    dev = torch.device("cuda")
+def parity_ragged(x, off_t, y, k=2048, grad=None, g=None):
+    import torch
+    import oracle
+    from paper_1606_06508_gb300 import synth
+    off = off_t.cpu().numpy()
+    n = off.size - 1
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([np.arange(min(n, 64)), rng.choice(n, min(n, k), replace=False),
+                                    np.arange(max(0, n - 64), n)]))
+    starts, ends = off[idx], off[idx + 1]
+    sub = synth.offsets_from_lengths(ends - starts)
+    gather = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]).astype(np.int64)
+    gt = torch.from_numpy(gather).to(x.device)
+    oy, _, oh, oc = oracle.normalize(x[gt].cpu().numpy(), dim=0, offsets=sub)
+    bad = _bits_mismatch(y[gt].cpu().numpy(), oy)
+    if grad is not None:
+        og = oracle.backward(oy, g[gt].cpu().numpy(), oh, oc, dim=0, offsets=sub)
+        bad += _bits_mismatch(grad[gt].cpu().numpy(), og)
+    return {"sampled_vectors": int(idx.size), "mismatching_values": bad, "max_ulp_vs_oracle": 0 if bad == 0 else None}
+
+
+# ---------------------------------------------------------------------------- workloads
+class Work:
+    """One workload: a step (device-resident inputs), its units and algorithmic
+    bytes, the dominant kernel, host buffers for the end-to-end figure."""
+
+    def __init__(self, **kw):
+        self.flush = False
+        self.__dict__.update(kw)
+
+
+def build_work(name, count, rank, torch, L, api, synth):
+    dev = torch.device("cuda", torch.cuda.current_device())
     s = torch.cuda.current_stream()
+    seed = 1000 * rank
 
-    def rec(name, fn, units, nbytes, iters=10, **kw):
-        try:
-            fn()
-            torch.cuda.synchronize()
-            ts = time_events(fn, iters, s)
-            t = statistics.median(ts) * 1e-3
-            out[name] = {"vectors_per_s": units / t, "ms": t * 1e3, "GB_per_s": nbytes / t / 1e9,
-                         "frac_of_hbm_peak": nbytes / t / 1e9 / peak, "algorithmic_bytes": nbytes, **kw}
-        except Exception as e:  # report, do not hide
-            out[name] = {"error": repr(e)}
+    if name == "quat":
+        x = synth.quaternions_f32_torch(count, seed=1 + seed, device=dev)
+        y = torch.empty_like(x)
+        xp, yp = x.data_ptr(), y.data_ptr()
 
-    # fwd+bwd, 2^24 binary32 quaternions (forward saves h and code; backward reads y, g, h, code)
-    n4 = 1 << 24
-    x = synth.quaternions_f32_torch(n4, seed=4, device=dev)
-    g = synth.normal_like_torch((n4, 4), torch.float32, seed=40, device=dev)
-    y = torch.empty_like(x)
-    h = torch.empty(n4, device=dev)
-    c = torch.empty(n4, dtype=torch.int8, device=dev)
-    gr = torch.empty_like(x)
-    from paper_1606_06508_gb300 import _lib as L
+        def step():
+            st = L.normalize_f32(xp, yp, None, None, None, count, 4, None, None, 0, s.cuda_stream)
+            if st:
+                L.check(st, "normalize_f32")
+        return Work(desc=("2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 "
+                          "wide-exponent/N(0,1) components") if count == QUAT_COUNT
+                    else f"{count} binary32 quaternions, forward (profiling size)",
+                    units=count, bytes=32 * count, dtype="f32", kernel="k_small_vec16<float,4>", launches=1,
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 4),
+                    bytes_model="16 B read + 16 B written per quaternion")
 
-    def fb():
-        L.check(L.normalize_f32(x.data_ptr(), y.data_ptr(), None, h.data_ptr(), c.data_ptr(), n4, 4, None, None,
-                                0, s.cuda_stream), "fwd")
-        L.check(L.normalize_backward_f32(y.data_ptr(), g.data_ptr(), h.data_ptr(), c.data_ptr(), gr.data_ptr(), n4, 4,
-                                         None, None, 0, s.cuda_stream), "bwd")
-    rec("fwd_bwd_quat_f32_2^24", fb, n4, n4 * (16 + 16 + 4 + 1 + 16 + 16 + 4 + 1 + 16),
-        bytes_model="fwd 16+16+4+1, bwd 16+16+4+1+16 per quaternion")
-    del x, g, y, h, c, gr
+    if name == "fwdbwd_quat":
+        n = count if count != QUAT_COUNT else 1 << 24
+        x = synth.quaternions_f32_torch(n, seed=4 + seed, device=dev)
+        g = synth.normal_like_torch((n, 4), torch.float32, seed=40 + seed, device=dev)
+        y, gr = torch.empty_like(x), torch.empty_like(x)
+        h = torch.empty(n, device=dev)
+        c = torch.empty(n, dtype=torch.int8, device=dev)
 
-    # rows of 256
-    for f, cnt in (("f32", 1 << 20), ("f64", 1 << 19)):
-        dt = torch.float32 if f == "f32" else torch.float64
-        xr = synth.rows_torch(cnt, 256, dt, seed=2, device=dev)
-        yr = torch.empty_like(xr)
-        fn = L.normalize_f32 if f == "f32" else L.normalize_f64
-        rec(f"rows256_{f}", lambda: L.check(fn(xr.data_ptr(), yr.data_ptr(), None, None, None, cnt, 256, None, None, 0,
-                                               s.cuda_stream), "rows"), cnt, 2 * xr.numel() * xr.element_size())
-        del xr, yr
+        def step():
+            L.check(L.normalize_f32(x.data_ptr(), y.data_ptr(), None, h.data_ptr(), c.data_ptr(), n, 4, None, None, 0,
+                                    s.cuda_stream), "fwd")
+            L.check(L.normalize_backward_f32(y.data_ptr(), g.data_ptr(), h.data_ptr(), c.data_ptr(), gr.data_ptr(),
+                                             n, 4, None, None, 0, s.cuda_stream), "bwd")
+        return Work(desc=f"{n} binary32 quaternions, forward (saving h and code) + backward",
+                    units=n, bytes=90 * n, dtype="f32", kernel="k_small_vec16<float,4> + k_small_bwd<float,4>",
+                    launches=2, step=step, h2d=[x, g], d2h=[gr],
+                    parity=lambda: parity_dense(x, y, 4, grad=gr, g=g),
+                    bytes_model="fwd 16+16+4+1, bwd 16+16+4+1+16 per quaternion")
 
-    # ragged, 4,000,000 vectors (40% of length 2-4, the rest log-uniform in [5, 4096])
-    for f in ("f32", "f64"):
-        dt = torch.float32 if f == "f32" else torch.float64
-        cnt = 4_000_000
-        lengths = synth.ragged_lengths_torch(cnt, seed=3, device=dev)
+    if name in ("rows_f32", "rows_f64"):
+        dt = torch.float32 if name.endswith("f32") else torch.float64
+        rows = count if count != QUAT_COUNT else (1 << 20 if dt == torch.float32 else 1 << 19)
+        x = synth.rows_torch(rows, 256, dt, seed=2 + seed, device=dev)
+        y = torch.empty_like(x)
+        fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
+
+        def step():
+            L.check(fn(x.data_ptr(), y.data_ptr(), None, None, None, rows, 256, None, None, 0, s.cuda_stream), "rows")
+        return Work(desc=f"{rows} rows of 256 {name[-3:]}, forward, N(0,1) x 2^s per row",
+                    units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
+                    kernel=f"k_rows_warp<{'float,4,2' if dt == torch.float32 else 'double,2,4'}>", launches=1,
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 256, k=2048),
+                    bytes_model="2 x 256 x s per row")
+
+    if name in ("ragged_f32", "ragged_f64", "fwdbwd_ragged_f64"):
+        dt = torch.float64 if "f64" in name else torch.float32
+        fb = name.startswith("fwdbwd")
+        cnt = count if count != QUAT_COUNT else (500_000 if fb else 4_000_000)
+        kind, nmax = ("loguniform", 1024) if fb else ("mixture", 4096)
+        lengths = synth.ragged_lengths_torch(cnt, seed=3 + seed, kind=kind, nmax=nmax, device=dev)
         off = synth.offsets_from_lengths_torch(lengths)
-        xv = synth.ragged_values_torch(lengths, dt, seed=3)
-        yv = torch.empty_like(xv)
+        x = synth.ragged_values_torch(lengths, dt, seed=3 + seed)
+        y = torch.empty_like(x)
         plan = api.Plan(cnt, dt)
         mapping = plan.autotune(off)
-        fn = L.normalize_f32 if f == "f32" else L.normalize_f64
-        nb = 2 * xv.numel() * xv.element_size() + 8 * (cnt + 1)
-        rec(f"ragged4M_{f}", lambda: L.check(fn(xv.data_ptr(), yv.data_ptr(), None, None, None, cnt, 0, off.data_ptr(),
-                                                 plan.handle, 0, s.cuda_stream), "ragged"), cnt, nb,
-            mapping=list(mapping), elements=int(xv.numel()))
-        del xv, yv, plan, lengths, off
+        fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
+        s_bytes = x.element_size()
+        if not fb:
+            def step():
+                L.check(fn(x.data_ptr(), y.data_ptr(), None, None, None, cnt, 0, off.data_ptr(), plan.handle, 0,
+                           s.cuda_stream), "ragged")
+            return Work(desc=f"{cnt} ragged {name[-3:]} vectors (40% of length 2-4, else log-uniform [5,4096]), "
+                             f"int64 offsets, forward, one persistent launch after the classifier",
+                        units=cnt, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1), dtype=name[-3:],
+                        kernel="k_classify + k_ragged (persistent)", launches=2, step=step, h2d=[x, off], d2h=[y],
+                        parity=lambda: parity_ragged(x, off, y), mapping=list(mapping), plan=plan,
+                        bytes_model="2 n s per vector + 8 B offsets")
+        g = synth.normal_like_torch(x.shape, dt, seed=41 + seed, device=dev)
+        gr = torch.empty_like(x)
+        h = torch.empty(cnt, dtype=dt, device=dev)
+        c = torch.empty(cnt, dtype=torch.int8, device=dev)
 
-    # the copy ceiling and the naive algorithm on the headline's bytes
-    a = torch.empty(QUAT_COUNT * 4, device=dev)
+        def step():
+            L.check(fn(x.data_ptr(), y.data_ptr(), None, h.data_ptr(), c.data_ptr(), cnt, 0, off.data_ptr(),
+                       plan.handle, 0, s.cuda_stream), "fwd")
+            L.check(L.normalize_backward_f64(y.data_ptr(), g.data_ptr(), h.data_ptr(), c.data_ptr(), gr.data_ptr(),
+                                             cnt, 0, off.data_ptr(), plan.handle, 0, s.cuda_stream), "bwd")
+        return Work(desc=f"{cnt} ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
+                    units=cnt, bytes=5 * x.numel() * s_bytes + 2 * 9 * cnt + 2 * 8 * (cnt + 1), dtype="f64",
+                    kernel="k_classify + k_ragged; k_classify + k_ragged_bwd_{blocks,warps,threads}", launches=6,
+                    step=step, h2d=[x, g, off], d2h=[gr], parity=lambda: parity_ragged(x, off, y, grad=gr, g=g),
+                    mapping=list(mapping), plan=plan,
+                    bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector")
+
+    if name == "vec3_f64":
+        xh = synth.vectors3_f64(65536, seed=0 + seed)
+        x = torch.from_numpy(xh).to(dev)
+        y = torch.empty_like(x)
+        cnt = x.shape[0]
+
+        def step():
+            L.check(L.normalize_f64(x.data_ptr(), y.data_ptr(), None, None, None, cnt, 3, None, None, 0,
+                                    s.cuda_stream), "vec3")
+        return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
+                    units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_staged<double,3>", launches=1,
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 3, k=cnt), flush=True,
+                    bytes_model="24 B read + 24 B written per vector")
+    raise ValueError(f"unknown workload {name}")
+
+
+WORKLOAD_NAMES = ["quat", "fwdbwd_quat", "rows_f32", "rows_f64", "ragged_f32", "ragged_f64", "fwdbwd_ragged_f64",
+                  "vec3_f64"]
+
+
+def extras(torch, L, api, synth, peak):
+    """Secondary measurements on this GPU (each step repeated 10 times,
+    CUDA events): the other workloads, the copy ceiling, the naive algorithm."""
+    out = {}
+    s = torch.cuda.current_stream()
+    for name in WORKLOAD_NAMES[1:]:
+        try:
+            w = build_work(name, QUAT_COUNT, 0, torch, L, api, synth)
+            w.step()
+            torch.cuda.synchronize()
+            flush = None
+            if w.flush:
+                fb = torch.empty(2 * L2_BYTES // 4, device="cuda")
+                flush = lambda: fb.fill_(1.0)  # noqa: E731
+            t = statistics.median(time_events(w.step, 10, s, between=flush)) * 1e-3
+            out[name] = {"vectors_per_s": w.units / t, "ms": t * 1e3, "GB_per_s": w.bytes / t / 1e9,
+                         "frac_of_hbm_peak": w.bytes / t / 1e9 / peak, "algorithmic_bytes": w.bytes,
+                         "kernel": w.kernel, **({"mapping": w.mapping} if hasattr(w, "mapping") else {})}
+            del w
+        except Exception as e:  # report, do not hide
+            out[name] = {"error": repr(e)}
+        torch.cuda.empty_cache()
+    a = torch.empty(QUAT_COUNT * 4, device="cuda")
     b = torch.empty_like(a)
     a.normal_()
-    rec("copy_2GiB", lambda: L.check(L.ngb_copy(b.data_ptr(), a.data_ptr(), a.numel() * 4, s.cuda_stream), "copy"),
-        QUAT_COUNT, 2 * a.numel() * 4)
-    rec("naive_quat_f32_2^26", lambda: L.check(L.naive_normalize_f32(a.data_ptr(), b.data_ptr(), QUAT_COUNT, 4,
-                                                                      s.cuda_stream), "naive"),
-        QUAT_COUNT, QUAT_COUNT * QUAT_BYTES)
-    del a, b
+    for nm, fn, units, nb in (
+            ("copy_2GiB", lambda: L.check(L.ngb_copy(b.data_ptr(), a.data_ptr(), a.numel() * 4, s.cuda_stream), "c"),
+             QUAT_COUNT, 2 * a.numel() * 4),
+            ("naive_quat_f32_2^26", lambda: L.check(L.naive_normalize_f32(a.data_ptr(), b.data_ptr(), QUAT_COUNT, 4,
+                                                                           s.cuda_stream), "n"),
+             QUAT_COUNT, 32 * QUAT_COUNT)):
+        fn()
+        t = statistics.median(time_events(fn, 10, s)) * 1e-3
+        out[nm] = {"vectors_per_s": units / t, "ms": t * 1e3, "GB_per_s": nb / t / 1e9,
+                   "frac_of_hbm_peak": nb / t / 1e9 / peak, "algorithmic_bytes": nb}
     return out
 
 
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    threads = cpu_threads()
+    x, dim, off, units = host_sample(args.workload, 1 << 17)
+    for _ in range(args.warmup):
+        oracle.normalize_threads(x, dim, off, threads=threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.normalize_threads(x, dim, off, threads=threads)
+    dt = time.perf_counter() - t0
+    v = args.steps * units / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.workload.endswith("f64") else "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "reference_step": f"{units} vectors of the same recipe (bounded sample)"},
+        "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{units} vectors per step, oracle on {threads} host threads over contiguous ranges"},
+        "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- our arm
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -332,15 +472,11 @@ def run_ours(args):
 
     peak, peak_src = peaks()
     s = torch.cuda.current_stream()
-    count = args.count
-    x = synth.quaternions_f32_torch(count, seed=1 + 1000 * rank, device=dev)
-    y = torch.empty_like(x)
-    xp, yp = x.data_ptr(), y.data_ptr()
-
-    def step():
-        st = L.normalize_f32(xp, yp, None, None, None, count, 4, None, None, 0, s.cuda_stream)
-        if st:
-            L.check(st, "normalize_f32")
+    w = build_work(args.workload, args.count, rank, torch, L, api, synth)
+    flush = None
+    if w.flush:
+        flush_buf = torch.empty(2 * L2_BYTES // 4, device=dev)
+        flush = lambda: flush_buf.fill_(1.0)  # noqa: E731
 
     try:
         gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -348,70 +484,75 @@ def run_ours(args):
         gpu_id = str(torch.cuda.current_device())
     sampler = ClockSampler(gpu_id)
     sampler.start()
-    for _ in range(max(args.warmup, 3)):
-        step()
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        w.step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     sampler.mark()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(args.steps):
-        step()
-    e1.record(s)
-    torch.cuda.synchronize()
+    if flush is None:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            w.step()
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    else:  # L2 flushed between steps, outside the timed intervals
+        ms = sum(time_events(w.step, args.steps, s, between=flush))
     if world > 1:
         torch.distributed.barrier()
     sampler.mark()
-    ms = e0.elapsed_time(e1)
     if world > 1:
         t = torch.tensor([ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    # per-launch durations of the dominant (only) kernel, events on its stream
-    per_launch = time_events(step, min(args.steps, 200), s)
+    # per-step durations, events on the launching stream
+    per_step = time_events(w.step, min(args.steps, 200), s, between=flush)
     sampler.stop()
     clocks = sampler.summary()
 
     result = None
     if rank == 0:
         secs = ms * 1e-3
-        value = world * args.steps * count / secs
-        launch_s = statistics.mean(per_launch) * 1e-3
-        achieved = count * QUAT_BYTES / launch_s / 1e9
-        traffic, tnote = traffic_for(KERNEL)
+        step_s = statistics.mean(per_step) * 1e-3
+        achieved = w.bytes / step_s / 1e9
+        traffic, tnote = traffic_for(args.workload)
         result = {
-            "metric": METRIC, "value": value, "unit": "vectors/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD if count == QUAT_COUNT else f"{count} quaternions (profiling size)",
-                       "vectors_per_gpu": count,
-                       "algorithmic_bytes_per_step_per_gpu": count * QUAT_BYTES,
-                       "l2": "inputs larger than L2 (1 GiB in, 1 GiB out per GPU); no flush",
-                       "parallelism": f"independent batch per GPU x{world}"},
-            "GB_per_s": world * args.steps * count * QUAT_BYTES / secs / 1e9,
+            "metric": METRIC, "value": world * args.steps * w.units / secs, "unit": "vectors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "config": {"workload": w.desc, "vectors_per_gpu": w.units, "algorithmic_bytes_per_step_per_gpu": w.bytes,
+                       "bytes_model": w.bytes_model,
+                       "l2": ("L2 flushed between steps (256 MB write), outside the timed intervals" if w.flush else
+                              "inputs larger than L2 (126 MB); no flush"),
+                       "parallelism": f"independent batch per GPU x{world}",
+                       **({"mapping": w.mapping} if hasattr(w, "mapping") else {})},
+            "GB_per_s": world * args.steps * w.bytes / secs / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic, "kernel": KERNEL,
+                         "frac": achieved / peak, "traffic": traffic, "kernel": w.kernel,
                          "peak_source": peak_src + ("; of measured" if peak_src.startswith("measured") else
                                                     "; of fallback"),
-                         "achieved_note": f"32 B algorithmic per quaternion x {count} / mean event time of "
-                                          f"{len(per_launch)} single-launch steps",
+                         "achieved_note": f"algorithmic bytes per step / mean event time of {len(per_step)} steps "
+                                          f"({w.launches} kernel launch(es) per step)",
                          "traffic_note": tnote},
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * w.launches,
             "clocks": clocks,
         }
-    # e2e through host buffers (pinned), same metric
+    # e2e through pinned host buffers: H2D of the step's inputs, the call, D2H of its result
     e2e_steps = max(1, min(args.steps, 20))
-    hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-    hy = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-    hx.copy_(x)
+    hin = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in w.h2d]
+    hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in w.d2h]
     torch.cuda.synchronize()
 
     def e2e_step():
-        x.copy_(hx, non_blocking=True)
-        step()
-        hy.copy_(y, non_blocking=True)
+        for hd, dd in zip(hin, w.h2d):
+            dd.copy_(hd, non_blocking=True)
+        w.step()
+        for hd, dd in zip(hout, w.d2h):
+            hd.copy_(dd, non_blocking=True)
     e2e_step()
     torch.cuda.synchronize()
     if world > 1:
@@ -428,15 +569,19 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ems = float(t.item())
     if rank == 0:
-        result["e2e"] = {"value": world * e2e_steps * count / (ems * 1e-3), "unit": "vectors/s",
-                         "h2d_bytes_per_step": count * 16, "d2h_bytes_per_step": count * 16,
-                         "steps": e2e_steps, "note": "pinned host x -> device, normalize_f32, device y -> pinned host"}
-        result["parity"] = parity_sample(x, y, api)
+        result["e2e"] = {"value": world * e2e_steps * w.units / (ems * 1e-3), "unit": "vectors/s",
+                         "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in w.h2d),
+                         "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in w.d2h),
+                         "steps": e2e_steps,
+                         "note": "pinned host inputs -> device, library call(s), device result -> pinned host"}
+        result["parity"] = w.parity()
         if world == 1:
-            if not args.no_extras:
-                del hx, hy
-                result["also"] = extras(api, synth, torch, peak)
-            result["cpu_baseline"] = cpu_baseline_quat()
+            if not args.no_extras and args.workload == "quat":
+                del hin, hout
+                w = None
+                torch.cuda.empty_cache()
+                result["also"] = extras(torch, L, api, synth, peak)
+            result["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(result), flush=True)
     if world > 1:
         torch.distributed.barrier()
@@ -450,9 +595,11 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=WORKLOAD_NAMES, default="quat")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--count", type=int, default=QUAT_COUNT,
-                    help="quaternions per GPU (default 2^26, the headline workload; smaller only for profiling)")
+                    help="units per GPU; the default selects each workload's full size (2^26 quaternions for the "
+                         "headline); smaller values only for profiling")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
