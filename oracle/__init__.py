@@ -26,7 +26,7 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 CODE_ONE, CODE_SMIN, CODE_SMAX, CODE_ZERO = 0, 1, 2, 3
 VECTOR_SEMANTICS = 1
-CR_SLOTS = 1024
+CR_SLOTS = 256
 MAX_LEN = 1 << 20
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fno-unsafe-math-optimizations",

@@ -28,7 +28,7 @@
  *   - the quaternion zero result [0,0,1,0] is q^ with r^ = 0, and callers
  *     may ask for the all-zero result instead (vector semantics);
  *   - n = 1 runs the Normalize2D steps on one component;
- *   - n >= 5 uses the summation order CR(n) and the constants
+ *   - n >= 5 uses the summation order CR(n) (256 slots) and the constants
  *     tau_max = 2^53 / 2^501, sigma_max = 2^-75 / 2^-523 (binary32 / 64);
  *   - the backward pass (no counterpart in the paper) is
  *     grad = ((g - y (y.g)) * h) * c.
@@ -47,7 +47,7 @@
 #define OR_CODE_ZERO 3 /* x = 0: the zero result, no factor */
 
 #define OR_VECTOR_SEMANTICS 1u /* n = 4: all-zero result for x = 0 */
-#define OR_CR_SLOTS 1024
+#define OR_CR_SLOTS 256
 #define OR_MAX_LEN (1 << 20)
 
 /* ---- binary32 (Table 2, single precision row) ---- */

@@ -38,7 +38,7 @@ def fr(v) -> Fr:
     return Fr(float(v))
 
 
-def cr_depth(n: int, slots: int = 1024) -> int:
+def cr_depth(n: int, slots: int = 256) -> int:
     """Roundings on the longest path of a term through the order CR(n): one
     product, the sequential additions inside a slot, and one per tree level."""
     used = min(n, slots)

@@ -138,7 +138,7 @@ def test_survey_closed_form_values(oracle_lib):
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])
-@pytest.mark.parametrize("n", [16, 64, 256, 1024, 1089, 4096])
+@pytest.mark.parametrize("n", [16, 64, 256, 289, 324, 529, 1024, 1089, 4096])
 def test_generic_exact_integer_norm(oracle_lib, f, n):
     """n equal components 2^j: every partial sum is an exact small integer times
     2^2j in any order, so r^ = sqrt(n) 2^j exactly and no term may be dropped
