@@ -125,9 +125,10 @@ ngb_status ngb_plan_create(ngb_plan** out, int64_t count, int32_t dtype_bytes, i
 ngb_status ngb_plan_destroy(ngb_plan* plan);
 
 /* The mapping: vectors with n <= thread_max (4..16) go one per thread, those
- * with n <= warp_max (thread_max..1024) one per warp, longer ones one per block
- * of block_threads (256 or 512) threads; grid_blocks persistent blocks
- * (0: one full wave).  Results do not depend on it. */
+ * with n <= warp_max (thread_max..NGB_MAX_LEN) one per warp, longer ones one
+ * per block of block_threads (128 or 256) threads; grid_blocks persistent
+ * blocks (0: one full wave).  Default 8, 8192, 256, 0.  Results do not depend
+ * on it. */
 ngb_status ngb_plan_set_mapping(ngb_plan* plan, int32_t thread_max, int32_t warp_max, int32_t block_threads,
                                 int32_t grid_blocks);
 ngb_status ngb_plan_get_mapping(const ngb_plan* plan, int32_t* thread_max, int32_t* warp_max,

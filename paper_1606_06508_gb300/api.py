@@ -64,7 +64,7 @@ class Plan:
         except Exception:
             pass
 
-    def set_mapping(self, thread_max=8, warp_max=1024, block_threads=256, grid_blocks=0):
+    def set_mapping(self, thread_max=8, warp_max=8192, block_threads=256, grid_blocks=0):
         L.check(L.ngb_plan_set_mapping(self.handle, thread_max, warp_max, block_threads, grid_blocks),
                 "ngb_plan_set_mapping")
 

@@ -60,7 +60,7 @@ struct ngb_plan {
   int device = 0;
   int32_t* buf = nullptr;  // counts[3], tickets[3], status, pad, items[3 * count]
   ngb::RaggedScratch sc{};
-  ngb::RaggedMapping map{8, 1024, 256, 0};
+  ngb::RaggedMapping map{8, 8192, 256, 0};
   bool graphs = true;
   cudaStream_t cap_stream = nullptr;
   struct Slot {
@@ -257,8 +257,9 @@ ngb_status ngb_plan_set_mapping(ngb_plan* p, int32_t thread_max, int32_t warp_ma
   g_last_error.clear();
   if (!p) return fail(NGB_ERR_INVALID_ARG, "plan is NULL");
   if (thread_max < 4 || thread_max > 16) return fail(NGB_ERR_INVALID_ARG, "thread_max must be in 4..16");
-  if (warp_max < thread_max || warp_max > 1024) return fail(NGB_ERR_INVALID_ARG, "warp_max must be in thread_max..1024");
-  if (block_threads != 256 && block_threads != 512) return fail(NGB_ERR_INVALID_ARG, "block_threads must be 256 or 512");
+  if (warp_max < thread_max || warp_max > NGB_MAX_LEN)
+    return fail(NGB_ERR_INVALID_ARG, "warp_max must be in thread_max..NGB_MAX_LEN");
+  if (block_threads != 128 && block_threads != 256) return fail(NGB_ERR_INVALID_ARG, "block_threads must be 128 or 256");
   if (grid_blocks < 0) return fail(NGB_ERR_INVALID_ARG, "grid_blocks < 0");
   p->map = ngb::RaggedMapping{thread_max, warp_max, block_threads, grid_blocks};
   return NGB_OK;
@@ -358,8 +359,8 @@ ngb_status ngb_plan_autotune(ngb_plan* p, const int64_t* offsets, const char* ca
   float best = 1e30f;
   ngb::RaggedMapping best_map = saved;
   const int tms[] = {4, 8, 16};
-  const int wms[] = {256, 512, 1024};
-  const int bts[] = {256, 512};
+  const int wms[] = {2048, 8192, 65536};
+  const int bts[] = {128, 256};
   ngb_status st = NGB_OK;
   for (int tm : tms)
     for (int wm : wms)

@@ -9,8 +9,8 @@
 //   5 <= dim <= 16     one vector per thread, order CR(n).
 //   17 <= dim <= 1024  one warp per row held in registers, 16-byte loads when
 //                      rows are 16-byte aligned.
-//   dim > 1024         one block per row (registers up to 4096, three passes
-//                      over the row beyond that).
+//   1024 < dim <= 16384  one warp per row streaming it (three passes).
+//   dim > 16384        one block of 256 threads per row streaming it.
 #pragma once
 #include "ngb_internal.h"
 #include "ngb_rowpath.cuh"
@@ -165,30 +165,44 @@ __global__ void __launch_bounds__(256) k_rows_warp_bwd(const T* __restrict__ y, 
     warp_backward<T, V, CH>(y + row * n, g + row * n, grad + row * n, n, lane, hs[row], cs[row]);
 }
 
-// dim > 1024, one block per row (CH = 0: three passes over the row).
-template <typename T, int B, int CH>
-__global__ void __launch_bounds__(B) k_rows_block(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
-                                                   int n) {
-  __shared__ BlockShared<T, B> sh;
-  for (int64_t row = blockIdx.x; row < count; row += gridDim.x) {
-    if (CH > 0)
-      block_forward<T, B, (CH > 0 ? CH : 1)>(x + row * n, y ? y + row * n : nullptr, n, out, row, sh);
-    else
-      block_forward_stream<T, B>(x + row * n, y ? y + row * n : nullptr, n, out, row, sh);
-  }
+// 1024 < dim <= 16384, one warp per row streaming it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_stream(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
+                                                      int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < count; row += nw)
+    warp_forward_stream<T>(x + row * n, y ? y + row * n : nullptr, n, lane, out, row);
 }
 
-template <typename T, int B, int CH>
-__global__ void __launch_bounds__(B) k_rows_block_bwd(const T* __restrict__ y, const T* __restrict__ g,
-                                                       const T* __restrict__ hs, const int8_t* __restrict__ cs,
-                                                       T* grad, int64_t count, int n) {
-  __shared__ BlockShared<T, B> sh;
-  for (int64_t row = blockIdx.x; row < count; row += gridDim.x) {
-    if (CH > 0)
-      block_backward<T, B, (CH > 0 ? CH : 1)>(y + row * n, g + row * n, grad + row * n, n, hs[row], cs[row], sh);
-    else
-      block_backward_stream<T, B>(y + row * n, g + row * n, grad + row * n, n, hs[row], cs[row], sh);
-  }
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_stream_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                          const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                          T* grad, int64_t count, int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t row = w0; row < count; row += nw)
+    warp_backward_stream<T>(y + row * n, g + row * n, grad + row * n, n, lane, hs[row], cs[row]);
+}
+
+// dim > 16384, one block of 256 threads per row streaming it.
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_block(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
+                                                     int n) {
+  __shared__ BlockShared<T, 256> sh;
+  for (int64_t row = blockIdx.x; row < count; row += gridDim.x)
+    block_forward_stream<T, 256>(x + row * n, y ? y + row * n : nullptr, n, out, row, sh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rows_block_bwd(const T* __restrict__ y, const T* __restrict__ g,
+                                                         const T* __restrict__ hs, const int8_t* __restrict__ cs,
+                                                         T* grad, int64_t count, int n) {
+  __shared__ BlockShared<T, 256> sh;
+  for (int64_t row = blockIdx.x; row < count; row += gridDim.x)
+    block_backward_stream<T, 256>(y + row * n, g + row * n, grad + row * n, n, hs[row], cs[row], sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,14 +310,11 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
       default: return launch_warp_rows<T, 1, 32>(x, y, out, count, dim, s);
     }
   }
-  if (dim <= 256 * 8) {
-    auto k = k_rows_block<T, 256, 8>;
-    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
-  } else if (dim <= 256 * 16) {
-    auto k = k_rows_block<T, 256, 16>;
-    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
+  if (dim <= 16384) {
+    auto k = k_rows_stream<T>;
+    k<<<grid_for(k, 256, count, 8), 256, 0, s>>>(x, y, out, count, dim);
   } else {
-    auto k = k_rows_block<T, 256, 0>;
+    auto k = k_rows_block<T>;
     k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
   }
   return cudaGetLastError();
@@ -345,14 +356,11 @@ cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const
       default: return launch_warp_rows_bwd<T, 1, 32>(y, g, h, c, grad, count, dim, s);
     }
   }
-  if (dim <= 256 * 8) {
-    auto k = k_rows_block_bwd<T, 256, 8>;
-    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
-  } else if (dim <= 256 * 16) {
-    auto k = k_rows_block_bwd<T, 256, 16>;
-    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
+  if (dim <= 16384) {
+    auto k = k_rows_stream_bwd<T>;
+    k<<<grid_for(k, 256, count, 8), 256, 0, s>>>(y, g, h, c, grad, count, dim);
   } else {
-    auto k = k_rows_block_bwd<T, 256, 0>;
+    auto k = k_rows_block_bwd<T>;
     k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(y, g, h, c, grad, count, dim);
   }
   return cudaGetLastError();

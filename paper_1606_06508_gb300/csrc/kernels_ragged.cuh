@@ -1,20 +1,22 @@
 // kernels_ragged.cuh -- ragged batches (vector i = x[offsets[i] .. offsets[i+1]))
-// in one persistent launch, forward and backward; instantiated per precision
-// by ragged_f32.cu and ragged_f64.cu.
+// forward and backward; instantiated per precision by ragged_f32.cu and
+// ragged_f64.cu.
 //
 // 1. k_classify reads the int64 offsets once, skips (and flags) vectors with
 //    bad offsets, finishes zero-length vectors (norm +0), and appends every
 //    other vector index to one of three lists by length: the block list
 //    (n > warp_max), the warp list (thread_max < n <= warp_max) and the thread
-//    list (n <= thread_max).  Appends are aggregated per block: one atomic per
-//    block and list.
-// 2. Forward: k_ragged runs one wave of persistent blocks that take work
-//    from the three lists in that order (longest vectors first) through
-//    atomic tickets, whole blocks on block items, warps on batches of warp
-//    items, lanes on thread items.  No block ever waits for another.
+//    list (n <= thread_max; n <= 4 always).  Appends are aggregated per block:
+//    one atomic per block and list.
+// 2. Forward: k_ragged runs one wave of persistent blocks that take work from
+//    the three lists in that order (longest vectors first) through atomic
+//    tickets: whole blocks on block items, warps on batches of warp items,
+//    lanes on thread items.  Warps and blocks stream their vector (three
+//    passes, a few partial sums per lane) instead of holding it, so the
+//    kernel keeps few registers and many loads in flight.  No block ever
+//    waits for another.
 // 3. Backward: one plain grid-stride kernel per list (k_ragged_bwd_blocks,
-//    k_ragged_bwd_warps, k_ragged_bwd_threads), each shaped like the dense
-//    backward kernels.
+//    k_ragged_bwd_warps, k_ragged_bwd_threads).
 // Every mapping evaluates the same operations in the same order (the paper's
 // Algorithms 3-7 for n <= 4, the order CR(n) for n >= 5), so the results do
 // not depend on the mapping, the grid or the order in which items are taken.
@@ -131,28 +133,6 @@ __device__ __forceinline__ void thread_item_bwd(const T* __restrict__ yr, const 
   }
 }
 
-template <typename T, int WCH>
-__device__ __forceinline__ void warp_item_fwd(const T* __restrict__ xr, T* yr, int n, int lane, const VecOut<T>& out,
-                                              int64_t vec) {
-  if (n <= 32) warp_forward<T, 1, 1>(xr, yr, n, lane, out, vec);
-  else if (n <= 64) warp_forward<T, 1, 2>(xr, yr, n, lane, out, vec);
-  else if (n <= 128) warp_forward<T, 1, 4>(xr, yr, n, lane, out, vec);
-  else if (n <= 256 || WCH <= 8) warp_forward<T, 1, (WCH < 8 ? WCH : 8)>(xr, yr, n, lane, out, vec);
-  else if (n <= 512 || WCH <= 16) warp_forward<T, 1, (WCH < 16 ? WCH : 16)>(xr, yr, n, lane, out, vec);
-  else warp_forward<T, 1, WCH>(xr, yr, n, lane, out, vec);
-}
-
-template <typename T, int WCH>
-__device__ __forceinline__ void warp_item_bwd(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
-                                              int lane, T h, int code) {
-  if (n <= 32) warp_backward<T, 1, 1>(yr, gr, gradr, n, lane, h, code);
-  else if (n <= 64) warp_backward<T, 1, 2>(yr, gr, gradr, n, lane, h, code);
-  else if (n <= 128) warp_backward<T, 1, 4>(yr, gr, gradr, n, lane, h, code);
-  else if (n <= 256 || WCH <= 8) warp_backward<T, 1, (WCH < 8 ? WCH : 8)>(yr, gr, gradr, n, lane, h, code);
-  else if (n <= 512 || WCH <= 16) warp_backward<T, 1, (WCH < 16 ? WCH : 16)>(yr, gr, gradr, n, lane, h, code);
-  else warp_backward<T, 1, WCH>(yr, gr, gradr, n, lane, h, code);
-}
-
 template <typename T>
 struct RaggedArgs {
   const T* x;          // forward input, or y for the backward pass
@@ -166,9 +146,8 @@ struct RaggedArgs {
   int64_t count;
 };
 
-// Forward persistent kernel.  WCH: chunks of 32 per lane for warp items
-// (warp_max <= 32 WCH).
-template <typename T, int B, int WCH>
+// Forward persistent kernel, B threads per block (128 or 256).
+template <typename T, int B>
 __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
   const int t = threadIdx.x, lane = t & 31;
@@ -187,10 +166,7 @@ __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
     const int64_t vec = Lb[it];
     const int64_t s = a.off[vec];
     const int n = (int)(a.off[vec + 1] - s);
-    T* yr = a.y ? a.y + s : nullptr;
-    if (n <= 8 * B) block_forward<T, B, 8>(a.x + s, yr, n, a.out, vec, sh);
-    else if (n <= 16 * B) block_forward<T, B, 16>(a.x + s, yr, n, a.out, vec, sh);
-    else block_forward_stream<T, B>(a.x + s, yr, n, a.out, vec, sh);
+    block_forward_stream<T, B>(a.x + s, a.y ? a.y + s : nullptr, n, a.out, vec, sh);
   }
 
   // warp items, WARP_BATCH per ticket
@@ -203,7 +179,7 @@ __global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
       const int64_t vec = Lw[base + j];
       const int64_t s = a.off[vec];
       const int n = (int)(a.off[vec + 1] - s);
-      warp_item_fwd<T, WCH>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+      warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
     }
   }
 
@@ -236,16 +212,12 @@ __global__ void __launch_bounds__(B) k_ragged_bwd_blocks(RaggedArgs<T> a) {
     const int64_t vec = Lb[it];
     const int64_t s = a.off[vec];
     const int n = (int)(a.off[vec + 1] - s);
-    const T h = a.h_in[vec];
-    const int code = a.c_in[vec];
-    if (n <= 8 * B) block_backward<T, B, 8>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
-    else if (n <= 16 * B) block_backward<T, B, 16>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
-    else block_backward_stream<T, B>(a.x + s, a.g + s, a.y + s, n, h, code, sh);
+    block_backward_stream<T, B>(a.x + s, a.g + s, a.y + s, n, a.h_in[vec], a.c_in[vec], sh);
   }
 }
 
 // Backward, warp list: one warp per vector, warp-stride over the list.
-template <typename T, int WCH>
+template <typename T>
 __global__ void __launch_bounds__(256) k_ragged_bwd_warps(RaggedArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int nwarp = a.sc.counts[1];
@@ -256,7 +228,7 @@ __global__ void __launch_bounds__(256) k_ragged_bwd_warps(RaggedArgs<T> a) {
     const int64_t vec = Lw[it];
     const int64_t s = a.off[vec];
     const int n = (int)(a.off[vec + 1] - s);
-    warp_item_bwd<T, WCH>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
+    warp_backward_stream<T>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
   }
 }
 
@@ -275,21 +247,6 @@ __global__ void __launch_bounds__(256) k_ragged_bwd_threads(RaggedArgs<T> a) {
 }
 
 // ---------------------------------------------------------------------------
-template <typename T, int B, int WCH>
-inline int full_wave_of() {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ragged<T, B, WCH>, B, 0);
-  if (per_sm < 1) per_sm = 1;
-  return per_sm * device_sm_count();
-}
-
-template <typename T>
-inline int full_wave_dispatch(const RaggedMapping& m) {
-  const bool big = m.warp_max > 512;
-  if (m.block_threads == 512) return big ? full_wave_of<T, 512, 32>() : full_wave_of<T, 512, 16>();
-  return big ? full_wave_of<T, 256, 32>() : full_wave_of<T, 256, 16>();
-}
-
 template <typename K>
 inline int wave_of(K kernel, int threads) {
   int per_sm = 0;
@@ -299,33 +256,28 @@ inline int wave_of(K kernel, int threads) {
 }
 
 template <typename T>
+inline int full_wave_dispatch(const RaggedMapping& m) {
+  return m.block_threads == 128 ? wave_of(k_ragged<T, 128>, 128) : wave_of(k_ragged<T, 256>, 256);
+}
+
+template <typename T>
 inline void launch_backward_lists(const RaggedArgs<T>& a, const RaggedMapping& m, cudaStream_t s) {
   const int cap = m.grid_blocks > 0 ? m.grid_blocks : 1 << 30;
   auto clamp = [cap](int g) { return g < cap ? g : cap; };
-  if (m.block_threads == 512) {
-    k_ragged_bwd_blocks<T, 512><<<clamp(wave_of(k_ragged_bwd_blocks<T, 512>, 512)), 512, 0, s>>>(a);
+  if (m.block_threads == 128) {
+    k_ragged_bwd_blocks<T, 128><<<clamp(wave_of(k_ragged_bwd_blocks<T, 128>, 128)), 128, 0, s>>>(a);
   } else {
     k_ragged_bwd_blocks<T, 256><<<clamp(wave_of(k_ragged_bwd_blocks<T, 256>, 256)), 256, 0, s>>>(a);
   }
-  if (m.warp_max > 512) {
-    k_ragged_bwd_warps<T, 32><<<clamp(wave_of(k_ragged_bwd_warps<T, 32>, 256)), 256, 0, s>>>(a);
-  } else {
-    k_ragged_bwd_warps<T, 16><<<clamp(wave_of(k_ragged_bwd_warps<T, 16>, 256)), 256, 0, s>>>(a);
-  }
+  k_ragged_bwd_warps<T><<<clamp(wave_of(k_ragged_bwd_warps<T>, 256)), 256, 0, s>>>(a);
   k_ragged_bwd_threads<T><<<clamp(wave_of(k_ragged_bwd_threads<T>, 256)), 256, 0, s>>>(a);
 }
 
 template <typename T>
 inline void launch_persistent(const RaggedArgs<T>& a, const RaggedMapping& m, cudaStream_t s) {
   const int grid = m.grid_blocks > 0 ? m.grid_blocks : full_wave_dispatch<T>(m);
-  const bool big = m.warp_max > 512;
-  if (m.block_threads == 512) {
-    if (big) k_ragged<T, 512, 32><<<grid, 512, 0, s>>>(a);
-    else k_ragged<T, 512, 16><<<grid, 512, 0, s>>>(a);
-  } else {
-    if (big) k_ragged<T, 256, 32><<<grid, 256, 0, s>>>(a);
-    else k_ragged<T, 256, 16><<<grid, 256, 0, s>>>(a);
-  }
+  if (m.block_threads == 128) k_ragged<T, 128><<<grid, 128, 0, s>>>(a);
+  else k_ragged<T, 256><<<grid, 256, 0, s>>>(a);
 }
 
 template <typename T>

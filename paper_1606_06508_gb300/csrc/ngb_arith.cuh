@@ -20,7 +20,9 @@ enum : int { CODE_ONE = 0, CODE_SIGMA_MIN = 1, CODE_SIGMA_MAX = 2, CODE_ZERO = 3
 // Canonical summation order for n >= 5: CR_SLOTS slots, slot j holding the
 // left-to-right sum of terms j, j + CR_SLOTS, ...; then a halving tree over
 // the slots with strides CR_SLOTS/2 .. 1, skipping slots that hold no term.
-constexpr int CR_SLOTS = 1024;
+// 256 slots: a warp streams any length with 8 partial sums per lane, and a
+// block of 256 threads holds one slot per thread.
+constexpr int CR_SLOTS = 256;
 constexpr int MAX_LEN = 1 << 20;
 
 template <typename T> struct FP;
@@ -86,6 +88,33 @@ template <typename T>
 __device__ __forceinline__ T scale_by(int code, T c, T x) {
   return code == CODE_ONE ? x : FP<T>::mul(c, x);
 }
+
+// Nonzero test on the bit pattern: +0 and -0 are zero, NaN is not.  Exact,
+// and it keeps the binary64 compares off the FP64 pipe.
+__device__ __forceinline__ bool is_nonzero(float v) { return (__float_as_uint(v) << 1) != 0u; }
+__device__ __forceinline__ bool is_nonzero(double v) {
+  return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) != 0ull;
+}
+
+// x~ = c x for c = 2^E != 1 (generic constants).  binary64: when x and c x are
+// both normal the product is exact and is formed by adding E to the exponent
+// field, which gives the bits of RN(c x); zeros, subnormals, infinities, NaN
+// and subnormal results take the multiplication.  binary32 multiplies.
+template <typename T> struct Pow2Scale;
+template <> struct Pow2Scale<float> {
+  __device__ __forceinline__ static float apply(float c, int /*E*/, float x) { return __fmul_rn(c, x); }
+  __device__ __forceinline__ static int exponent(int code) { return code == CODE_SIGMA_MIN ? 100 : -75; }
+};
+template <> struct Pow2Scale<double> {
+  __device__ __forceinline__ static double apply(double c, int E, double x) {
+    const long long b = __double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    const int ne = e + E;
+    if (e != 0 && e != 0x7ff && ne > 0 && ne < 0x7ff) return __longlong_as_double(b + ((long long)E << 52));
+    return __dmul_rn(c, x);
+  }
+  __device__ __forceinline__ static int exponent(int code) { return code == CODE_SIGMA_MIN ? 592 : -523; }
+};
 
 // ---------------------------------------------------------------------------
 // The largest magnitude of n <= 4 components in the branch order of Scale2D
@@ -229,7 +258,7 @@ __device__ __forceinline__ int normalize_thread_generic(const T* __restrict__ xr
   for (int k = 0; k < NMAX; ++k) {
     v[k] = k < n ? xr[k] : T(0);
     if (k < n) {
-      nz |= !(v[k] == T(0));
+      nz |= is_nonzero(v[k]);
       m = FP<T>::fmax(m, FP<T>::abs(v[k]));
     }
   }

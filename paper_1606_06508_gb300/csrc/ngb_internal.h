@@ -27,9 +27,9 @@ cudaError_t launch_fixed_backward(const T* y, const T* g, const T* h, const int8
 // Ragged batches: bucket lists produced by the classifier, consumed by one
 // persistent kernel.
 struct RaggedMapping {
-  int thread_max;     // n <= thread_max: one thread per vector (<= 16)
-  int warp_max;       // thread_max < n <= warp_max: one warp per vector (<= 1024)
-  int block_threads;  // n > warp_max: one block of this many threads per vector (256 or 512)
+  int thread_max;     // n <= thread_max: one thread per vector (4 .. 16)
+  int warp_max;       // thread_max < n <= warp_max: one warp per vector, streamed
+  int block_threads;  // n > warp_max: one block of this many threads per vector (128 or 256)
   int grid_blocks;    // persistent grid size; 0 = one full wave
 };
 

@@ -2,8 +2,8 @@
 // generic (n >= 5) scaling normalization and of its backward pass.
 //
 // The sum of squares (and the backward dot product) follows the canonical
-// order CR(n): slot j < 1024 is the left-to-right sum of terms j, j + 1024, ...,
-// then slot j <- slot j + slot (j + s) for s = 512, 256, ..., 1 whenever slot
+// order CR(n): slot j < 256 is the left-to-right sum of terms j, j + 256, ...,
+// then slot j <- slot j + slot (j + s) for s = 128, 64, ..., 1 whenever slot
 // j + s holds a term.  Each mapping places the slots so that every tree level
 // becomes either an in-register add, a warp shuffle (xor by a power of two)
 // or one shared-memory exchange, and performs the levels in the same
@@ -48,11 +48,11 @@ template <> struct Vec<double, 2> {
 };
 
 // ---------------------------------------------------------------------------
-// Warp layout.  Lane l holds chunk c (c < CH) as the V elements
-// k = 32 V c + V l + e, e < V.  Slot j = k for k < 1024, so with G = 1024/(32V)
-// chunk groups: strides >= 32V pair chunk c with c + s/(32V) inside a lane,
-// strides V .. 16V pair lane l with lane l ^ (s/V), and strides < V pair
-// element e with e + s inside a lane.  Elements k >= 1024 are added in
+// Warp layout (row held in registers).  Lane l holds chunk c (c < CH) as the
+// V elements k = 32 V c + V l + e, e < V.  Slot j = k mod 256, so with
+// G = 256/(32V) chunk groups: strides >= 32V pair chunk c with c + s/(32V)
+// inside a lane, strides V .. 16V pair lane l with lane l ^ (s/V), and strides
+// < V pair element e with e + s inside a lane.  Chunks c >= G are added in
 // ascending order into the accumulator of chunk c mod G.
 // Requires n <= 32 V CH; for V > 1 also n % V == 0 and 16-byte aligned rows.
 template <typename T, int V, int CH>
@@ -67,7 +67,7 @@ __device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
     for (int e = 0; e < V; ++e)
       if (32 * V * c + V * lane + e < n) q[c % G][e] = FP<T>::add(q[c % G][e], q[c][e]);
   }
-  // strides 512 .. 32V: chunk c += chunk c + p
+  // strides 128 .. 32V: chunk c += chunk c + p
 #pragma unroll
   for (int p = G / 2; p >= 1; p >>= 1) {
 #pragma unroll
@@ -118,7 +118,7 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
 #pragma unroll
     for (int e = 0; e < V; ++e) {
       if (k0 + e < n) {
-        nz |= !(v[c][e] == T(0));
+        nz |= is_nonzero(v[c][e]);
         m = FP<T>::fmax(m, FP<T>::abs(v[c][e]));
       }
     }
@@ -212,12 +212,12 @@ __device__ __forceinline__ void warp_backward(const T* __restrict__ yr, const T*
 }
 
 // ---------------------------------------------------------------------------
-// Block layout (B threads, B a power of two in [64, 1024]).  Thread t holds
-// the elements k = B c + t.  Slot j = k mod 1024 belongs to thread j mod B,
-// as its accumulator j / B (G = 1024 / B of them): strides >= B are
-// in-thread, the remaining strides B/2 .. 1 run in warp 0 after one pass
-// through shared memory (lane l takes slots l + 32 i: strides B/2 .. 32
-// in-lane, then shuffles 16 .. 1).
+// Block layout (B threads, B = 64, 128 or 256).  Thread t holds the elements
+// k = B c + t.  Slot j = k mod 256 belongs to thread j mod B, as its
+// accumulator j / B (G = 256 / B of them): strides >= B are in-thread, the
+// remaining strides B/2 .. 1 run in warp 0 after one pass through shared
+// memory (lane l takes slots l + 32 i: strides B/2 .. 32 in-lane, then
+// shuffles 16 .. 1).
 template <typename T, int B>
 struct BlockShared {
   T slot[B];
@@ -276,7 +276,7 @@ __device__ __forceinline__ T block_cr_finish(T acc0, int used, BlockShared<T, B>
 }
 
 // In-thread part of the tree: accumulators of chunk c (c < CH) into slot
-// group c mod G, then strides 512 .. B.
+// group c mod G, then strides 128 .. B.
 template <typename T, int B, int CH>
 __device__ __forceinline__ T block_cr_tree(T (&q)[CH], int n, BlockShared<T, B>& sh) {
   constexpr int G = CR_SLOTS / B;
@@ -308,7 +308,7 @@ __device__ __forceinline__ void block_forward(const T* __restrict__ xr, T* yr, i
     const int k = B * c + t;
     v[c] = k < n ? __ldcs(xr + k) : T(0);
     if (k < n) {
-      nz |= !(v[c] == T(0));
+      nz |= is_nonzero(v[c]);
       m = FP<T>::fmax(m, FP<T>::abs(v[c]));
     }
   }
@@ -353,7 +353,7 @@ __device__ __forceinline__ void block_forward_stream(const T* __restrict__ xr, T
   T m = T(0);
   for (int k = t; k < n; k += B) {
     const T a = xr[k];
-    nz |= !(a == T(0));
+    nz |= is_nonzero(a);
     m = FP<T>::fmax(m, FP<T>::abs(a));
   }
   nz = __syncthreads_or(nz);
@@ -459,6 +459,158 @@ __device__ __forceinline__ void block_backward_stream(const T* __restrict__ yr, 
   const T dot = block_cr_finish<T, B>(acc[0], used, sh);
   for (int k = t; k < n; k += B)
     gradr[k] = FP<T>::mul(FP<T>::mul(FP<T>::sub(gr[k], FP<T>::mul(yr[k], dot)), h), cf);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming warp layout (any length).  Lane l reads the elements
+// k = 32 c + l, c = 0, 1, ..., eight chunks (256 elements) per round; slot
+// k mod 256 = 32 (c mod 8) + l is lane l's partial sum acc[c mod 8],
+// accumulated in ascending c.  Tree: strides 128, 64, 32 inside the lane,
+// 16 .. 1 by shuffles.  Nothing of the vector is held between passes: each
+// pass reads it again (the second and third reads usually hit L2).
+template <typename T>
+__device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+#pragma unroll
+  for (int p = 4; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int i = 0; i < p; ++i)
+      if (32 * (i + p) + lane < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
+  }
+#pragma unroll
+  for (int p = 16; p >= 1; p >>= 1) {
+    const T o = __shfl_xor_sync(FULL, acc[0], p);
+    if (lane < p && lane + p < used) acc[0] = FP<T>::add(acc[0], o);
+  }
+  return __shfl_sync(FULL, acc[0], 0);
+}
+
+template <typename T>
+__device__ __forceinline__ void stream_load8(const T* __restrict__ p, int base, int n, int lane, T (&v)[8]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int k = base + 32 * i + lane;
+    v[i] = k < n ? p[k] : T(0);
+  }
+}
+
+// Pass 2 of the forward: the scaled squares in the order CR(n).  SCALED
+// selects x~ = c x; otherwise x~ = x (c = 1).
+template <typename T, bool SCALED>
+__device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n, int lane, T cf, int E) {
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = T(0);
+  for (int base = 0; base < n; base += 256) {
+    T v[8];
+    stream_load8(xr, base, n, lane, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
+      const T q = FP<T>::mul(t, t);
+      if (base == 0) acc[i] = q;  // slots beyond n are never read by the tree
+      else if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q);
+    }
+  }
+  return stream_tree<T>(acc, n, lane);
+}
+
+// Pass 3 of the forward: x^ = h x~, written with evict-first stores.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
+  for (int base = 0; base < n; base += 256) {
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = base + 32 * i + lane;
+      v[i] = k < n ? __ldcs(xr + k) : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = base + 32 * i + lane;
+      if (k < n) __stcs(yr + k, FP<T>::mul(h, SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i]));
+    }
+  }
+}
+
+// Forward, one warp per vector of any length (5 <= n <= 2^20), three passes
+// over the vector: (1) largest magnitude and zero test, (2) scaled squares,
+// (3) outputs.  yr may be null (norm only).
+template <typename T>
+__device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
+                                                    const VecOut<T>& out, int64_t vec) {
+  T m = T(0);
+  bool nz = false;
+  for (int base = 0; base < n; base += 256) {
+    T v[8];
+    stream_load8(xr, base, n, lane, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      nz |= is_nonzero(v[i]);
+      m = FP<T>::fmax(m, FP<T>::abs(v[i]));
+    }
+  }
+  m = warp_fmax(m);
+  nz = __any_sync(FULL, nz);
+  if (!nz) {
+    if (yr)
+      for (int k = lane; k < n; k += 32) __stcs(yr + k, T(0));
+    if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
+    return;
+  }
+  const int code = select_code<T, true>(m);
+  const T cf = factor_of<T, true>(code);
+  const int E = Pow2Scale<T>::exponent(code);
+  const bool scaled = code != CODE_ONE;
+  const T rt = FP<T>::sqrt(scaled ? stream_sum_squares<T, true>(xr, n, lane, cf, E)
+                                  : stream_sum_squares<T, false>(xr, n, lane, cf, E));
+  const T h = FP<T>::rcp(rt);
+  if (yr) {
+    if (scaled) stream_write<T, true>(xr, yr, n, lane, h, cf, E);
+    else stream_write<T, false>(xr, yr, n, lane, h, cf, E);
+  }
+  if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),
+// (2) grad_k = ((g_k - y_k dot) h) c.
+template <typename T>
+__device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr,
+                                                     int n, int lane, T h, int code) {
+  if (code == CODE_ZERO) {
+    for (int k = lane; k < n; k += 32) __stcs(gradr + k, T(0));
+    return;
+  }
+  const T cf = factor_of<T, true>(code);
+  T acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = T(0);
+  for (int base = 0; base < n; base += 256) {
+    T a[8], b[8];
+    stream_load8(yr, base, n, lane, a);
+    stream_load8(gr, base, n, lane, b);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const T q = FP<T>::mul(a[i], b[i]);
+      if (base == 0) acc[i] = q;
+      else if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q);
+    }
+  }
+  const T dot = stream_tree<T>(acc, n, lane);
+  for (int base = 0; base < n; base += 256) {
+    T a[8], b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = base + 32 * i + lane;
+      a[i] = k < n ? __ldcs(yr + k) : T(0);
+      b[i] = k < n ? __ldcs(gr + k) : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = base + 32 * i + lane;
+      if (k < n) __stcs(gradr + k, FP<T>::mul(FP<T>::mul(FP<T>::sub(b[i], FP<T>::mul(a[i], dot)), h), cf));
+    }
+  }
 }
 
 }  // namespace ngb

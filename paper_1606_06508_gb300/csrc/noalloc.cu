@@ -63,7 +63,7 @@ extern "C" ngb_status normalize_ragged_f32_noalloc(const float* x, float* y, flo
   sc.tickets = base + 3;
   sc.status = base + 6;
   sc.items = base + 8;
-  ngb::RaggedMapping map{8, 1024, 256, 0};
+  ngb::RaggedMapping map{8, 8192, 256, 0};
   map.grid_blocks = ngb::ragged_full_wave<float>(map, false);
   e = ngb::launch_ragged<float>(x, y, norm, saved_h, saved_code, nullptr, nullptr, nullptr, nullptr, offsets, count,
                                 0, (flags & NGB_VALIDATE_OFFSETS) != 0, map, sc, false,
