@@ -146,9 +146,14 @@ struct RaggedArgs {
   int64_t count;
 };
 
-// Forward persistent kernel, B threads per block (128 or 256).
+// Forward persistent kernel, B threads per block (128 or 256).  Resident
+// threads per SM requested: 5 x 256 for binary32 (at most 48 registers),
+// 3 x 256 for binary64 (at most 80, no spills).
+template <typename T>
+constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 3 * 256 / B; }
+
 template <typename T, int B>
-__global__ void __launch_bounds__(B) k_ragged(RaggedArgs<T> a) {
+__global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
   const int t = threadIdx.x, lane = t & 31;
   const int nblk = a.sc.counts[0], nwarp = a.sc.counts[1], nthr = a.sc.counts[2];

@@ -89,9 +89,10 @@ __device__ __forceinline__ T scale_by(int code, T c, T x) {
   return code == CODE_ONE ? x : FP<T>::mul(c, x);
 }
 
-// Nonzero test on the bit pattern: +0 and -0 are zero, NaN is not.  Exact,
-// and it keeps the binary64 compares off the FP64 pipe.
-__device__ __forceinline__ bool is_nonzero(float v) { return (__float_as_uint(v) << 1) != 0u; }
+// Nonzero test: +0 and -0 are zero, NaN is not.  binary32 compares (one
+// predicate instruction); binary64 tests the bit pattern, which keeps the
+// compare off the FP64 pipe.
+__device__ __forceinline__ bool is_nonzero(float v) { return !(v == 0.0f); }
 __device__ __forceinline__ bool is_nonzero(double v) {
   return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) != 0ull;
 }

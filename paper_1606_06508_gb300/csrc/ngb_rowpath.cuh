@@ -485,12 +485,19 @@ __device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
   return __shfl_sync(FULL, acc[0], 0);
 }
 
+// Eight chunks of one round; rounds that lie inside the vector skip the
+// per-element bounds test.
 template <typename T>
 __device__ __forceinline__ void stream_load8(const T* __restrict__ p, int base, int n, int lane, T (&v)[8]) {
+  if (base + 256 <= n) {
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int k = base + 32 * i + lane;
-    v[i] = k < n ? p[k] : T(0);
+    for (int i = 0; i < 8; ++i) v[i] = p[base + 32 * i + lane];
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = base + 32 * i + lane;
+      v[i] = k < n ? p[k] : T(0);
+    }
   }
 }
 
@@ -501,15 +508,33 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
   T acc[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) acc[i] = T(0);
-  for (int base = 0; base < n; base += 256) {
+  {  // first round: one term per slot (slots beyond n are never read by the tree)
+    T v[8];
+    stream_load8(xr, 0, n, lane, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
+      acc[i] = FP<T>::mul(t, t);
+    }
+  }
+  int base = 256;
+  for (; base + 256 <= n; base += 256) {  // full rounds
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = xr[base + 32 * i + lane];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
+      acc[i] = FP<T>::add(acc[i], FP<T>::mul(t, t));
+    }
+  }
+  if (base < n) {  // last, partial round
     T v[8];
     stream_load8(xr, base, n, lane, v);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
-      const T q = FP<T>::mul(t, t);
-      if (base == 0) acc[i] = q;  // slots beyond n are never read by the tree
-      else if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q);
+      if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], FP<T>::mul(t, t));
     }
   }
   return stream_tree<T>(acc, n, lane);
@@ -518,7 +543,16 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
 // Pass 3 of the forward: x^ = h x~, written with evict-first stores.
 template <typename T, bool SCALED>
 __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
-  for (int base = 0; base < n; base += 256) {
+  int base = 0;
+  for (; base + 256 <= n; base += 256) {
+    T v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __ldcs(xr + base + 32 * i + lane);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      __stcs(yr + base + 32 * i + lane, FP<T>::mul(h, SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i]));
+  }
+  if (base < n) {
     T v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
