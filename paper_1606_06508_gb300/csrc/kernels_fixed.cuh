@@ -7,9 +7,8 @@
 //                      binary64 pairs), otherwise a 256-vector tile staged
 //                      through shared memory with 16-byte loads.
 //   5 <= dim <= 16     one vector per thread, order CR(n).
-//   17 <= dim <= 1024  one warp per row held in registers (coalesced scalar
-//                      loads: one value per lane goes through the shuffle
-//                      levels of the summation tree).
+//   17 <= dim <= 1024  one warp per row held in registers, 16-byte loads when
+//                      rows are 16-byte aligned.
 //   1024 < dim <= 16384  one warp per row streaming it (three passes).
 //   dim > 16384        one block of 256 threads per row streaming it.
 #pragma once
@@ -277,6 +276,7 @@ cudaError_t launch_warp_rows_bwd(const T* y, const T* g, const T* h, const int8_
 template <typename T>
 cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t count, int dim, bool quat_zero,
                                       cudaStream_t s) {
+  constexpr int W = 16 / sizeof(T);
   switch (dim) {
     case 1: return launch_small_fwd<T, 1>(x, y, out, count, false, s);
     case 2: return launch_small_fwd<T, 2>(x, y, out, count, false, s);
@@ -291,6 +291,15 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
     return cudaGetLastError();
   }
   if (dim <= 1024) {
+    if ((dim % W == 0) && aligned16(x) && aligned16(y)) {
+      switch (chunks_for(dim, 32 * W)) {
+        case 1: return launch_warp_rows<T, W, 1>(x, y, out, count, dim, s);
+        case 2: return launch_warp_rows<T, W, 2>(x, y, out, count, dim, s);
+        case 4: return launch_warp_rows<T, W, 4>(x, y, out, count, dim, s);
+        case 8: return launch_warp_rows<T, W, 8>(x, y, out, count, dim, s);
+        default: return launch_warp_rows<T, W, 32 / W>(x, y, out, count, dim, s);
+      }
+    }
     switch (chunks_for(dim, 32)) {
       case 1: return launch_warp_rows<T, 1, 1>(x, y, out, count, dim, s);
       case 2: return launch_warp_rows<T, 1, 2>(x, y, out, count, dim, s);
@@ -313,6 +322,7 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
 template <typename T>
 cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
                                        int dim, cudaStream_t s) {
+  constexpr int W = 16 / sizeof(T);
   switch (dim) {
     case 1: return launch_small_bwd<T, 1>(y, g, h, c, grad, count, s);
     case 2: return launch_small_bwd<T, 2>(y, g, h, c, grad, count, s);
@@ -326,6 +336,15 @@ cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const
     return cudaGetLastError();
   }
   if (dim <= 1024) {
+    if ((dim % W == 0) && aligned16(y) && aligned16(g) && aligned16(grad)) {
+      switch (chunks_for(dim, 32 * W)) {
+        case 1: return launch_warp_rows_bwd<T, W, 1>(y, g, h, c, grad, count, dim, s);
+        case 2: return launch_warp_rows_bwd<T, W, 2>(y, g, h, c, grad, count, dim, s);
+        case 4: return launch_warp_rows_bwd<T, W, 4>(y, g, h, c, grad, count, dim, s);
+        case 8: return launch_warp_rows_bwd<T, W, 8>(y, g, h, c, grad, count, dim, s);
+        default: return launch_warp_rows_bwd<T, W, 32 / W>(y, g, h, c, grad, count, dim, s);
+      }
+    }
     switch (chunks_for(dim, 32)) {
       case 1: return launch_warp_rows_bwd<T, 1, 1>(y, g, h, c, grad, count, dim, s);
       case 2: return launch_warp_rows_bwd<T, 1, 2>(y, g, h, c, grad, count, dim, s);

@@ -79,13 +79,23 @@ __device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
       }
     }
   }
-  // strides 16V .. V: lane l += lane l + p
+  // strides 16V .. V: lane l += lane l + p.  When every slot holds a term the
+  // level is a butterfly on all lanes: lane l and lane l ^ p both form the
+  // same sum (addition is commutative), so no lane needs a predicate.
+  if (used == CR_SLOTS) {
 #pragma unroll
-  for (int p = 16; p >= 1; p >>= 1) {
+    for (int p = 16; p >= 1; p >>= 1) {
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      const T o = __shfl_xor_sync(FULL, q[0][e], p);
-      if (lane < p && V * (lane + p) + e < used) q[0][e] = FP<T>::add(q[0][e], o);
+      for (int e = 0; e < V; ++e) q[0][e] = FP<T>::add(q[0][e], __shfl_xor_sync(FULL, q[0][e], p));
+    }
+  } else {
+#pragma unroll
+    for (int p = 16; p >= 1; p >>= 1) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) {
+        const T o = __shfl_xor_sync(FULL, q[0][e], p);
+        if (lane < p && V * (lane + p) + e < used) q[0][e] = FP<T>::add(q[0][e], o);
+      }
     }
   }
   // strides V/2 .. 1 inside lane 0
@@ -95,6 +105,7 @@ __device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
     for (int e = 0; e < p; ++e)
       if (e + p < used) q[0][e] = FP<T>::add(q[0][e], q[0][e + p]);
   }
+  if (used == CR_SLOTS) return q[0][0];  // the butterfly left the total in every lane
   return __shfl_sync(FULL, q[0][0], 0);
 }
 
@@ -141,14 +152,19 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
   }
   const int code = select_code<T, true>(m);
   const T cf = factor_of<T, true>(code);
+  if (code != CODE_ONE) {  // warp-uniform: no multiply when c = 1
+    const int E = Pow2Scale<T>::exponent(code);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[c][e] = Pow2Scale<T>::apply(cf, E, v[c][e]);
+    }
+  }
   T q[CH][V];
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      v[c][e] = scale_by(code, cf, v[c][e]);
-      q[c][e] = FP<T>::mul(v[c][e], v[c][e]);
-    }
+    for (int e = 0; e < V; ++e) q[c][e] = FP<T>::mul(v[c][e], v[c][e]);
   }
   const T rt = FP<T>::sqrt(warp_cr_tree<T, V, CH>(q, n, lane));
   const T h = FP<T>::rcp(rt);
@@ -476,6 +492,11 @@ __device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
 #pragma unroll
     for (int i = 0; i < p; ++i)
       if (32 * (i + p) + lane < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
+  }
+  if (used == CR_SLOTS) {  // butterfly: every lane ends with the total
+#pragma unroll
+    for (int p = 16; p >= 1; p >>= 1) acc[0] = FP<T>::add(acc[0], __shfl_xor_sync(FULL, acc[0], p));
+    return acc[0];
   }
 #pragma unroll
   for (int p = 16; p >= 1; p >>= 1) {
