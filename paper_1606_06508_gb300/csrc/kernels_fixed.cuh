@@ -276,7 +276,10 @@ cudaError_t launch_warp_rows_bwd(const T* y, const T* g, const T* h, const int8_
 template <typename T>
 cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t count, int dim, bool quat_zero,
                                       cudaStream_t s) {
-  constexpr int W = 16 / sizeof(T);
+  // binary32 rows use 16-byte loads; binary64 rows use 8-byte loads, whose
+  // slot layout needs fewer additions in the summation tree (5 shuffle levels
+  // and 7 in-lane additions instead of 5 x 2 and 7)
+  constexpr int W = sizeof(T) == 4 ? 4 : 1;
   switch (dim) {
     case 1: return launch_small_fwd<T, 1>(x, y, out, count, false, s);
     case 2: return launch_small_fwd<T, 2>(x, y, out, count, false, s);
@@ -291,7 +294,7 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
     return cudaGetLastError();
   }
   if (dim <= 1024) {
-    if ((dim % W == 0) && aligned16(x) && aligned16(y)) {
+    if (W > 1 && (dim % W == 0) && aligned16(x) && aligned16(y)) {
       switch (chunks_for(dim, 32 * W)) {
         case 1: return launch_warp_rows<T, W, 1>(x, y, out, count, dim, s);
         case 2: return launch_warp_rows<T, W, 2>(x, y, out, count, dim, s);
@@ -322,7 +325,10 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
 template <typename T>
 cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
                                        int dim, cudaStream_t s) {
-  constexpr int W = 16 / sizeof(T);
+  // binary32 rows use 16-byte loads; binary64 rows use 8-byte loads, whose
+  // slot layout needs fewer additions in the summation tree (5 shuffle levels
+  // and 7 in-lane additions instead of 5 x 2 and 7)
+  constexpr int W = sizeof(T) == 4 ? 4 : 1;
   switch (dim) {
     case 1: return launch_small_bwd<T, 1>(y, g, h, c, grad, count, s);
     case 2: return launch_small_bwd<T, 2>(y, g, h, c, grad, count, s);
@@ -336,7 +342,7 @@ cudaError_t launch_fixed_backward_impl(const T* y, const T* g, const T* h, const
     return cudaGetLastError();
   }
   if (dim <= 1024) {
-    if ((dim % W == 0) && aligned16(y) && aligned16(g) && aligned16(grad)) {
+    if (W > 1 && (dim % W == 0) && aligned16(y) && aligned16(g) && aligned16(grad)) {
       switch (chunks_for(dim, 32 * W)) {
         case 1: return launch_warp_rows_bwd<T, W, 1>(y, g, h, c, grad, count, dim, s);
         case 2: return launch_warp_rows_bwd<T, W, 2>(y, g, h, c, grad, count, dim, s);

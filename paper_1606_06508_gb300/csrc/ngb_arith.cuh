@@ -54,6 +54,7 @@ template <> struct FP<double> {
   static constexpr double tau_min = 0x1p-482, sigma_min = 0x1p592, inv_sigma_min = 0x1p-592;
   static constexpr double tau_max = 0x1p510, sigma_max = 0x1p-514, inv_sigma_max = 0x1p514;
   static constexpr double tau_max_n = 0x1p501, sigma_max_n = 0x1p-523, inv_sigma_max_n = 0x1p523;
+  static constexpr int tau_min_exp = -482, tau_max_n_exp = 501;  // log2 of tau_min, tau_max_n
 };
 
 // The factor choice of Scale2D/Scale3D/Normalize4D: compare the largest
@@ -89,13 +90,66 @@ __device__ __forceinline__ T scale_by(int code, T c, T x) {
   return code == CODE_ONE ? x : FP<T>::mul(c, x);
 }
 
-// Nonzero test: +0 and -0 are zero, NaN is not.  binary32 compares (one
-// predicate instruction); binary64 tests the bit pattern, which keeps the
-// compare off the FP64 pipe.
-__device__ __forceinline__ bool is_nonzero(float v) { return !(v == 0.0f); }
-__device__ __forceinline__ bool is_nonzero(double v) {
-  return (static_cast<unsigned long long>(__double_as_longlong(v)) << 1) != 0ull;
-}
+// Largest magnitude of a vector of n >= 5 components, for the factor choice
+// with the generic constants, and the zero test.  It only has to decide
+// m >= tau_min, m <= tau_max and "every component is zero", with m the
+// largest |x_k| over the components that are not NaN.
+//   binary32: m = fmax over |x_k| (fmax skips a NaN operand) and a nonzero flag.
+//   binary64: integer keys, so that no FP64 instruction runs per component.
+//     key(x) = (high word of |x|) | (low word != 0), maxed as unsigned.  tau_min
+//     and tau_max are powers of two: low word zero, even high word h(tau).
+//     Then |x| >= tau <=> key >= h(tau) and |x| > tau <=> key > h(tau), so the
+//     largest key decides both comparisons for m; the vector is zero iff the
+//     largest key is 0; and a NaN component (key > h(+inf)) is detected, after
+//     which the caller takes the keys again with NaN components counted as 0.
+template <typename T> struct MagTrack;
+
+template <> struct MagTrack<float> {
+  float m = 0.0f;
+  bool nz = false;
+  __device__ __forceinline__ void take(float v) {
+    nz |= !(v == 0.0f);
+    m = fmaxf(m, fabsf(v));
+  }
+  __device__ __forceinline__ void take_skip_nan(float v) { take(v); }
+  __device__ __forceinline__ void merge(const MagTrack& o) {
+    nz |= o.nz;
+    m = fmaxf(m, o.m);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    nz = __any_sync(0xffffffffu, nz);
+  }
+  __device__ __forceinline__ bool zero() const { return !nz; }
+  __device__ __forceinline__ bool has_nan() const { return false; }
+  __device__ __forceinline__ int code() const { return select_code<float, true>(m); }
+};
+
+template <> struct MagTrack<double> {
+  static constexpr uint32_t HI_INF = 0x7FF00000u;
+  static constexpr uint32_t HI_TMIN = (uint32_t)(FP<double>::tau_min_exp + 1023) << 20;
+  static constexpr uint32_t HI_TMAX = (uint32_t)(FP<double>::tau_max_n_exp + 1023) << 20;
+  uint32_t k = 0;
+  __device__ __forceinline__ static uint32_t key(double v) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
+    const uint32_t lo = (uint32_t)b;
+    return ((uint32_t)(b >> 32) & 0x7FFFFFFFu) | (lo < 1u ? lo : 1u);
+  }
+  __device__ __forceinline__ void take(double v) { k = max(k, key(v)); }
+  __device__ __forceinline__ void take_skip_nan(double v) {
+    const uint32_t t = key(v);
+    k = max(k, t > HI_INF ? 0u : t);
+  }
+  __device__ __forceinline__ void merge(const MagTrack& o) { k = max(k, o.k); }
+  __device__ __forceinline__ void warp_reduce() { k = __reduce_max_sync(0xffffffffu, k); }
+  __device__ __forceinline__ bool zero() const { return k == 0u; }
+  __device__ __forceinline__ bool has_nan() const { return k > HI_INF; }
+  __device__ __forceinline__ int code() const {
+    if (k >= HI_TMIN) return k <= HI_TMAX ? CODE_ONE : CODE_SIGMA_MAX;
+    return CODE_SIGMA_MIN;
+  }
+};
 
 // x~ = c x for c = 2^E != 1 (generic constants).  binary64: when x and c x are
 // both normal the product is exact and is formed by adding E to the exponent
@@ -253,24 +307,26 @@ __device__ __forceinline__ T cr_sum_thread(T (&q)[NMAX], int n) {
 template <typename T, int NMAX>
 __device__ __forceinline__ int normalize_thread_generic(const T* __restrict__ xr, T* yr, int n, T& r, T& h) {
   T v[NMAX];
-  bool nz = false;
-  T m = T(0);
+  MagTrack<T> mt;
 #pragma unroll
   for (int k = 0; k < NMAX; ++k) {
     v[k] = k < n ? xr[k] : T(0);
-    if (k < n) {
-      nz |= is_nonzero(v[k]);
-      m = FP<T>::fmax(m, FP<T>::abs(v[k]));
-    }
+    if (k < n) mt.take(v[k]);
   }
-  if (!nz) {
+  if (mt.zero()) {
     if (yr)
       for (int k = 0; k < n; ++k) yr[k] = T(0);
     r = T(0);
     h = T(0);
     return CODE_ZERO;
   }
-  const int code = select_code<T, true>(m);
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+#pragma unroll
+    for (int k = 0; k < NMAX; ++k)
+      if (k < n) mt.take_skip_nan(v[k]);
+  }
+  const int code = mt.code();
   const T c = factor_of<T, true>(code);
   T q[NMAX];
 #pragma unroll

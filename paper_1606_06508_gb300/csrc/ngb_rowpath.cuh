@@ -115,8 +115,7 @@ template <typename T, int V, int CH>
 __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
                                              const VecOut<T>& out, int64_t vec) {
   T v[CH][V];
-  bool nz = false;
-  T m = T(0);
+  MagTrack<T> mt;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int k0 = 32 * V * c + V * lane;
@@ -127,16 +126,10 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
       for (int e = 0; e < V; ++e) v[c][e] = T(0);
     }
 #pragma unroll
-    for (int e = 0; e < V; ++e) {
-      if (k0 + e < n) {
-        nz |= is_nonzero(v[c][e]);
-        m = FP<T>::fmax(m, FP<T>::abs(v[c][e]));
-      }
-    }
+    for (int e = 0; e < V; ++e) mt.take(v[c][e]);  // zero padding changes neither m nor the zero test
   }
-  m = warp_fmax(m);
-  nz = __any_sync(FULL, nz);
-  if (!nz) {  // every component compares equal to zero
+  mt.warp_reduce();
+  if (mt.zero()) {  // every component compares equal to zero
     if (yr) {
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
@@ -150,7 +143,16 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
     if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
     return;
   }
-  const int code = select_code<T, true>(m);
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) mt.take_skip_nan(v[c][e]);
+    }
+    mt.warp_reduce();
+  }
+  const int code = mt.code();
   const T cf = factor_of<T, true>(code);
   if (code != CODE_ONE) {  // warp-uniform: no multiply when c = 1
     const int E = Pow2Scale<T>::exponent(code);
@@ -239,6 +241,7 @@ struct BlockShared {
   T slot[B];
   T red[B / 32];
   T total;
+  uint32_t kred[B / 32];
   int item;
   int flag;
 };
@@ -258,6 +261,25 @@ __device__ __forceinline__ T block_fmax(T m, BlockShared<T, B>& sh) {
   const T r = sh.total;
   __syncthreads();
   return r;
+}
+
+// MagTrack over the block; every thread gets the result.
+template <int B>
+__device__ __forceinline__ void block_reduce_mag(MagTrack<float>& mt, BlockShared<float, B>& sh) {
+  mt.nz = __syncthreads_or(mt.nz);
+  mt.m = block_fmax<float, B>(mt.m, sh);
+}
+template <int B>
+__device__ __forceinline__ void block_reduce_mag(MagTrack<double>& mt, BlockShared<double, B>& sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t k = __reduce_max_sync(FULL, mt.k);
+  if (lane == 0) sh.kred[w] = k;
+  __syncthreads();
+  uint32_t r = sh.kred[0];
+#pragma unroll
+  for (int i = 1; i < B / 32; ++i) r = max(r, sh.kred[i]);
+  __syncthreads();
+  mt.k = r;
 }
 
 // acc[i] holds slot i B + t of thread t (strides >= B already applied by the
@@ -317,20 +339,15 @@ __device__ __forceinline__ void block_forward(const T* __restrict__ xr, T* yr, i
                                               int64_t vec, BlockShared<T, B>& sh) {
   const int t = threadIdx.x;
   T v[CH];
-  bool nz = false;
-  T m = T(0);
+  MagTrack<T> mt;
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int k = B * c + t;
     v[c] = k < n ? __ldcs(xr + k) : T(0);
-    if (k < n) {
-      nz |= is_nonzero(v[c]);
-      m = FP<T>::fmax(m, FP<T>::abs(v[c]));
-    }
+    mt.take(v[c]);
   }
-  nz = __syncthreads_or(nz);
-  m = block_fmax<T, B>(m, sh);
-  if (!nz) {
+  block_reduce_mag<B>(mt, sh);
+  if (mt.zero()) {
     if (yr) {
 #pragma unroll
       for (int c = 0; c < CH; ++c)
@@ -339,7 +356,13 @@ __device__ __forceinline__ void block_forward(const T* __restrict__ xr, T* yr, i
     if (t == 0) out.put(vec, T(0), T(0), CODE_ZERO);
     return;
   }
-  const int code = select_code<T, true>(m);
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+#pragma unroll
+    for (int c = 0; c < CH; ++c) mt.take_skip_nan(v[c]);
+    block_reduce_mag<B>(mt, sh);
+  }
+  const int code = mt.code();
   const T cf = factor_of<T, true>(code);
   T q[CH];
 #pragma unroll
@@ -365,22 +388,21 @@ __device__ __forceinline__ void block_forward_stream(const T* __restrict__ xr, T
                                                      int64_t vec, BlockShared<T, B>& sh) {
   constexpr int G = CR_SLOTS / B;
   const int t = threadIdx.x;
-  bool nz = false;
-  T m = T(0);
-  for (int k = t; k < n; k += B) {
-    const T a = xr[k];
-    nz |= is_nonzero(a);
-    m = FP<T>::fmax(m, FP<T>::abs(a));
-  }
-  nz = __syncthreads_or(nz);
-  m = block_fmax<T, B>(m, sh);
-  if (!nz) {
+  MagTrack<T> mt;
+  for (int k = t; k < n; k += B) mt.take(xr[k]);
+  block_reduce_mag<B>(mt, sh);
+  if (mt.zero()) {
     if (yr)
       for (int k = t; k < n; k += B) yr[k] = T(0);
     if (t == 0) out.put(vec, T(0), T(0), CODE_ZERO);
     return;
   }
-  const int code = select_code<T, true>(m);
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+    for (int k = t; k < n; k += B) mt.take_skip_nan(xr[k]);
+    block_reduce_mag<B>(mt, sh);
+  }
+  const int code = mt.code();
   const T cf = factor_of<T, true>(code);
   T acc[G];
 #pragma unroll
@@ -594,26 +616,26 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
 template <typename T>
 __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
                                                     const VecOut<T>& out, int64_t vec) {
-  T m = T(0);
-  bool nz = false;
+  MagTrack<T> mt;
   for (int base = 0; base < n; base += 256) {
     T v[8];
     stream_load8(xr, base, n, lane, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      nz |= is_nonzero(v[i]);
-      m = FP<T>::fmax(m, FP<T>::abs(v[i]));
-    }
+    for (int i = 0; i < 8; ++i) mt.take(v[i]);  // zero padding changes neither m nor the zero test
   }
-  m = warp_fmax(m);
-  nz = __any_sync(FULL, nz);
-  if (!nz) {
+  mt.warp_reduce();
+  if (mt.zero()) {
     if (yr)
       for (int k = lane; k < n; k += 32) __stcs(yr + k, T(0));
     if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
     return;
   }
-  const int code = select_code<T, true>(m);
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+    for (int k = lane; k < n; k += 32) mt.take_skip_nan(xr[k]);
+    mt.warp_reduce();
+  }
+  const int code = mt.code();
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
   const bool scaled = code != CODE_ONE;
