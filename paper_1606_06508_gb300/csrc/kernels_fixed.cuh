@@ -166,6 +166,28 @@ __global__ void __launch_bounds__(256) k_rows_warp_bwd(const T* __restrict__ y, 
 }
 
 // 1024 < dim <= 16384, one warp per row streaming it.
+// binary64 rows of 17 <= dim <= 16384: one warp streams NB consecutive rows
+// and shares one square root and reciprocal among them.
+constexpr int F64_ROW_BATCH = 4;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) k_rows_stream_batch(const T* __restrict__ x, T* y, VecOut<T> out,
+                                                            int64_t count, int n) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = w0 * NB; g < count; g += nw * NB) {
+    const int nb = (int)((count - g) < NB ? (count - g) : NB);
+    auto item = [&](int j, const T*& xr, T*& yr, int& nn, int64_t& vec) {
+      vec = g + j;
+      xr = x + vec * n;
+      yr = y ? y + vec * n : nullptr;
+      nn = n;
+    };
+    warp_forward_stream_batch<T, NB, MAX_LEN>(item, nb, lane, out);
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_rows_stream(const T* __restrict__ x, T* y, VecOut<T> out, int64_t count,
                                                       int n) {
@@ -291,6 +313,11 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
     auto k = k_rows_thread<T>;
     const int grid = grid_for(k, 256, count, 256);
     k<<<grid, 256, 0, s>>>(x, y, out, count, dim);
+    return cudaGetLastError();
+  }
+  if (sizeof(T) == 8 && dim <= 16384) {
+    auto k = k_rows_stream_batch<T, F64_ROW_BATCH>;
+    k<<<grid_for(k, 256, (count + F64_ROW_BATCH - 1) / F64_ROW_BATCH, 8), 256, 0, s>>>(x, y, out, count, dim);
     return cudaGetLastError();
   }
   if (dim <= 1024) {

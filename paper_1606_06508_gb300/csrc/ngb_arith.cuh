@@ -13,6 +13,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ngb_f64emu.cuh"
+
 namespace ngb {
 
 enum : int { CODE_ONE = 0, CODE_SIGMA_MIN = 1, CODE_SIGMA_MAX = 2, CODE_ZERO = 3 };
@@ -124,6 +126,7 @@ template <> struct MagTrack<float> {
   __device__ __forceinline__ bool zero() const { return !nz; }
   __device__ __forceinline__ bool has_nan() const { return false; }
   __device__ __forceinline__ int code() const { return select_code<float, true>(m); }
+  __device__ __forceinline__ bool emu_ok(int /*code*/) const { return false; }
 };
 
 template <> struct MagTrack<double> {
@@ -131,23 +134,48 @@ template <> struct MagTrack<double> {
   static constexpr uint32_t HI_TMIN = (uint32_t)(FP<double>::tau_min_exp + 1023) << 20;
   static constexpr uint32_t HI_TMAX = (uint32_t)(FP<double>::tau_max_n_exp + 1023) << 20;
   uint32_t k = 0;
+  uint32_t kmin1 = 0xFFFFFFFFu;  // min over components of key - 1: zero components wrap to the top
   __device__ __forceinline__ static uint32_t key(double v) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v));
     const uint32_t lo = (uint32_t)b;
     return ((uint32_t)(b >> 32) & 0x7FFFFFFFu) | (lo < 1u ? lo : 1u);
   }
-  __device__ __forceinline__ void take(double v) { k = max(k, key(v)); }
-  __device__ __forceinline__ void take_skip_nan(double v) {
+  __device__ __forceinline__ void take(double v) {
+    const uint32_t t = key(v);
+    k = max(k, t);
+    kmin1 = min(kmin1, t - 1u);
+  }
+  __device__ __forceinline__ void take_skip_nan(double v) {  // also rules out the integer-pipe steps
     const uint32_t t = key(v);
     k = max(k, t > HI_INF ? 0u : t);
+    kmin1 = 0u;
   }
-  __device__ __forceinline__ void merge(const MagTrack& o) { k = max(k, o.k); }
-  __device__ __forceinline__ void warp_reduce() { k = __reduce_max_sync(0xffffffffu, k); }
+  __device__ __forceinline__ void merge(const MagTrack& o) {
+    k = max(k, o.k);
+    kmin1 = min(kmin1, o.kmin1);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+    k = __reduce_max_sync(0xffffffffu, k);
+    kmin1 = __reduce_min_sync(0xffffffffu, kmin1);
+  }
   __device__ __forceinline__ bool zero() const { return k == 0u; }
   __device__ __forceinline__ bool has_nan() const { return k > HI_INF; }
   __device__ __forceinline__ int code() const {
     if (k >= HI_TMIN) return k <= HI_TMAX ? CODE_ONE : CODE_SIGMA_MAX;
     return CODE_SIGMA_MIN;
+  }
+  // Whether the integer-pipe scale and squares (Chunk<double, N, true>) take
+  // every component of the vector for the factor c = 2^E of `code`: no NaN or
+  // infinity, and every nonzero component normal with 2^-511 <= |c x_k| <
+  // 2^512.  The upper bound holds for every factor choice (|c x_k| <= 2^501
+  // with c = 1, < 2^501 with sigma_max, < 2^110 with sigma_min); the lower
+  // bound is |x_k| >= 2^(-511 - E), i.e. key >= (512 - E) << 20, and at least
+  // the smallest normal number.
+  __device__ __forceinline__ bool emu_ok(int code) const {
+    const int E = code == CODE_ONE ? 0 : (code == CODE_SIGMA_MIN ? 592 : -523);
+    const int p = 512 - E;
+    const uint32_t tmin = p > 1 ? (uint32_t)p << 20 : (1u << 20);
+    return k < HI_INF && kmin1 >= tmin - 1u;
   }
 };
 
@@ -169,6 +197,59 @@ template <> struct Pow2Scale<double> {
     return __dmul_rn(c, x);
   }
   __device__ __forceinline__ static int exponent(int code) { return code == CODE_SIGMA_MIN ? 592 : -523; }
+};
+
+// Chunk operations of the long-vector paths, N values per thread:
+//   scale:   v_i <- c v_i with c = 2^E != 1 (exact in every case the paper
+//            allows: the factor only moves the exponent)
+//   squares: q_i <- RN(v_i * v_i)
+// EMU = false: the hardware multiplication.  EMU = true (binary64 only): the
+// integer-pipe forms, exponent addition for the scale and f64emu::square for
+// the squares; the caller takes this form only for a vector whose components
+// are all in their range (MagTrack<double>::emu_ok), so no component needs a
+// fallback and no FP64 instruction is issued for these steps.
+// Of every 8 outputs x^_k = h x~_k of a binary64 vector on the integer-pipe
+// path, how many are formed by f64emu::mul (the rest by the FP64 pipe): the
+// two pipes run side by side, and this split balances them.
+constexpr int F64_EMU_OUTPUTS_OF_8 = 4;
+
+template <typename T, int N, bool EMU> struct Chunk {
+  __device__ __forceinline__ static void scale(T c, int /*E*/, T (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = FP<T>::mul(c, v[i]);
+  }
+  __device__ __forceinline__ static void squares(const T (&v)[N], T (&q)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) q[i] = FP<T>::mul(v[i], v[i]);
+  }
+  __device__ __forceinline__ static T output(int /*i*/, T h, T v) { return FP<T>::mul(h, v); }
+};
+template <int N> struct Chunk<double, N, true> {
+  __device__ __forceinline__ static void scale(double /*c*/, int E, double (&v)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v[i]));
+      const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+      const bool zero = ((hi << 1) | lo) == 0u;  // c (+-0) = +-0
+      const uint32_t nhi = zero ? hi : hi + ((uint32_t)E << 20);
+      v[i] = __longlong_as_double(static_cast<long long>(((unsigned long long)nhi << 32) | lo));
+    }
+  }
+  __device__ __forceinline__ static void squares(const double (&v)[N], double (&q)[N]) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const uint64_t a = static_cast<uint64_t>(__double_as_longlong(v[i])) & 0x7FFFFFFFFFFFFFFFull;
+      q[i] = __longlong_as_double(static_cast<long long>(f64emu::square(a)));
+    }
+  }
+  // x^ = RN(h x~) for chunk position i (h = 1/r~ lies in [2^-511, 2^482] and
+  // h x~ in [2^-1022, 1] for these vectors, inside f64emu::mul's range)
+  __device__ __forceinline__ static double output(int i, double h, double v) {
+    if ((i & 7) < F64_EMU_OUTPUTS_OF_8)
+      return __longlong_as_double(static_cast<long long>(
+          f64emu::mul(static_cast<uint64_t>(__double_as_longlong(v)), static_cast<uint64_t>(__double_as_longlong(h)))));
+    return __dmul_rn(h, v);
+  }
 };
 
 // ---------------------------------------------------------------------------

@@ -37,38 +37,99 @@ NGB_HD uint64_t round_shift(uint64_t v, int k) {
   return (v + ((uint64_t(1) << (k - 1)) - 1u) + lsb) >> k;
 }
 
-// a * a for a = |x| (sign bit clear).  Fast path: x normal and the square
-// normal without overflow (biased exponent of the square in [1, 2046]).
+NGB_HD uint32_t funnel_r(uint32_t lo, uint32_t hi, uint32_t n) {  // (hi:lo) >> n, 0 < n < 32
+#if defined(__CUDA_ARCH__)
+  return __funnelshift_r(lo, hi, n);
+#else
+  return (uint32_t)((((uint64_t)hi << 32) | lo) >> n);
+#endif
+}
+
+// a * a for a = |x| (sign bit clear), valid when x = 0, or x is normal and
+// its square is normal (square_in_range).
 //
 // With x = m 2^(e-1075), m = 2^52 + f, the square is m^2 2^(2e-2150) and
-// m^2 lies in [2^104, 2^106).  m^2 is formed exactly from three 32 x 32-bit
-// products of m = mh 2^32 + ml:  m^2 = mh^2 2^64 + (mh ml) 2^33 + ml^2.
-// The significand keeps the top 53 bits (k = 52 or 53 bits are rounded off)
-// and the biased exponent is 2e - 1023 (k = 52) or 2e - 1022 (k = 53).
-// Adding the significand, hidden bit included, to (exponent - 1) << 52 packs
-// the result; a rounding carry to 2^53 moves into the exponent by itself.
-// A square is never a tie that rounds up: a tie needs k = 53 and m = 2^26 o
-// with o odd, and then the last kept place, bit 53 of m^2 = 2^52 o^2, is bit 1
-// of o^2, which is 0 because o^2 = 1 (mod 8).  So adding 2^(k-1) - 1 and
-// truncating rounds to nearest even.
-NGB_HD uint64_t square(uint64_t a, bool& ok) {
-  const int e = (int)(a >> 52);
-  const uint32_t ml = (uint32_t)a;
-  const uint32_t mh = ((uint32_t)(a >> 32) & 0xFFFFFu) | 0x100000u;
-  const uint64_t ll = (uint64_t)ml * ml;
-  const uint64_t hl = (uint64_t)mh * ml;
-  const uint64_t hh = (uint64_t)mh * mh;
-  const uint64_t L = ll + (hl << 33);
-  uint64_t H = hh + (hl >> 31) + (L < ll ? 1u : 0u);  // H < 2^42
-  const int s = (int)(H >> 41);                        // m^2 >= 2^105
-  const int k = 52 + s;
-  // round (H, L) >> k: k <= 53, so the rounding increment touches L only
-  const uint64_t L2 = L + ((uint64_t(1) << (k - 1)) - 1u);
-  H += (L2 < L ? 1u : 0u);
-  const uint64_t sig = (H << (64 - k)) | (L2 >> k);  // in [2^52, 2^53]
-  const int E0 = 2 * e - 1024 + s;                   // biased exponent - 1
-  ok = (e != 0) && (E0 >= 0) && (E0 <= 2044);
-  return ((uint64_t)(uint32_t)E0 << 52) + sig;
+// m^2 lies in [2^104, 2^106).  m^2 is formed exactly, as four 32-bit words,
+// from three 32 x 32-bit products of m = mh 2^32 + ml:
+//     m^2 = mh^2 2^64 + (2 mh ml) 2^32 + ml^2.
+// The significand keeps the top 53 bits: k = 52 + s bits are rounded off,
+// s = 1 when m^2 >= 2^105, and the biased exponent is 2e - 1023 + s.
+// Rounding: a square is never a tie that rounds up (a tie needs
+// m^2 = 2^(k-1) o^2 with o odd, and then the last kept bit, bit k, is bit 1
+// of o^2, which is 0 because o^2 = 1 (mod 8)), so adding 2^(k-1) - 1 and
+// truncating rounds to nearest even.  The low word only contributes its
+// carry (w0 != 0) to that addition.  Adding the significand, hidden bit
+// included, to (exponent - 1) << 52 packs the result; a rounding carry to
+// 2^53 moves into the exponent by itself.
+NGB_HD uint64_t square(uint64_t a) {
+  const uint32_t hi = (uint32_t)(a >> 32), lo = (uint32_t)a;
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+  const uint64_t ll = (uint64_t)lo * lo;
+  const uint64_t hl2 = (uint64_t)(mh << 1) * lo;  // 2 mh ml < 2^54
+  const uint64_t hh = (uint64_t)mh * mh;          // < 2^42
+  const uint32_t w0 = (uint32_t)ll;
+  const uint64_t t1 = (ll >> 32) + (uint32_t)hl2;
+  const uint64_t t2 = (t1 >> 32) + (hl2 >> 32) + (uint32_t)hh;
+  const uint32_t w1 = (uint32_t)t1, w2 = (uint32_t)t2;
+  const uint32_t w3 = (uint32_t)(t2 >> 32) + (uint32_t)(hh >> 32);  // < 2^10
+  const uint32_t s = w3 >> 9;
+  const uint64_t u1 = (uint64_t)w1 + ((0x80000u << s) - 1u) + (w0 != 0 ? 1u : 0u);
+  const uint64_t u2 = (uint64_t)w2 + (uint32_t)(u1 >> 32);
+  const uint32_t v3 = w3 + (uint32_t)(u2 >> 32);
+  const uint32_t sh = 20u + s;
+  const uint32_t sig_lo = funnel_r((uint32_t)u1, (uint32_t)u2, sh);
+  const uint32_t sig_hi = funnel_r((uint32_t)u2, v3, sh);  // < 2^22, hidden bit at 2^20
+  const uint32_t e = hi >> 20;
+  const uint32_t rhi = sig_hi + ((2u * e + s - 1024u) << 20);
+  return e == 0 ? 0 : (((uint64_t)rhi << 32) | sig_lo);
+}
+
+// The operands square() takes: x = 0, or x normal with a normal square
+// (2^-511 <= |x| < 2^512).
+NGB_HD bool square_in_range(uint64_t a) {
+  const uint32_t e = (uint32_t)(a >> 52);
+  return a == 0 || (e >= 512u && e <= 1534u);
+}
+
+// x * y for y > 0, rounded to nearest even, valid when x = +-0 or x and y are
+// normal and |x y| is normal without overflow (mul_in_range).  The same word
+// arithmetic as square(), with four 32 x 32-bit products
+//     mx my = (xh yh) 2^64 + (xh yl + xl yh) 2^32 + xl yl
+// and ties possible: the rounding adds 2^(k-1) - 1 + (bit k), which carries
+// into bit k exactly when the discarded part is above half a unit, or equal
+// to it with bit k odd.  The sign is that of x.
+NGB_HD uint64_t mul(uint64_t x, uint64_t y) {
+  const uint32_t xh = (uint32_t)(x >> 32), xl = (uint32_t)x;
+  const uint32_t yh = (uint32_t)(y >> 32), yl = (uint32_t)y;
+  const uint32_t mxh = (xh & 0xFFFFFu) | 0x100000u, myh = (yh & 0xFFFFFu) | 0x100000u;
+  const uint64_t ll = (uint64_t)xl * yl;
+  const uint64_t lh = (uint64_t)xl * myh;  // < 2^53
+  const uint64_t hl = (uint64_t)mxh * yl;  // < 2^53
+  const uint64_t hh = (uint64_t)mxh * myh; // < 2^42
+  const uint32_t w0 = (uint32_t)ll;
+  const uint64_t t1 = (ll >> 32) + (uint32_t)lh + (uint32_t)hl;
+  const uint64_t t2 = (t1 >> 32) + (lh >> 32) + (hl >> 32) + (uint32_t)hh;
+  const uint32_t w1 = (uint32_t)t1, w2 = (uint32_t)t2;
+  const uint32_t w3 = (uint32_t)(t2 >> 32) + (uint32_t)(hh >> 32);  // < 2^10
+  const uint32_t s = w3 >> 9;
+  const uint32_t sh = 20u + s;
+  const uint32_t lsb = (w1 >> sh) & 1u;
+  const uint64_t u1 = (uint64_t)w1 + ((0x80000u << s) - 1u) + (lsb | (w0 != 0 ? 1u : 0u));
+  const uint64_t u2 = (uint64_t)w2 + (uint32_t)(u1 >> 32);
+  const uint32_t v3 = w3 + (uint32_t)(u2 >> 32);
+  const uint32_t sig_lo = funnel_r((uint32_t)u1, (uint32_t)u2, sh);
+  const uint32_t sig_hi = funnel_r((uint32_t)u2, v3, sh);
+  const uint32_t ex = (xh >> 20) & 0x7FFu, ey = yh >> 20;
+  const uint32_t rhi = (sig_hi + ((ex + ey + s - 1024u) << 20)) | (xh & 0x80000000u);
+  return ex == 0 ? (x & 0x8000000000000000ull) : (((uint64_t)rhi << 32) | sig_lo);
+}
+
+// The operands mul() takes (y > 0): x = +-0, or x and y normal with a normal
+// product: the biased exponent ex + ey - 1023 (+1) of x y within [1, 2046].
+NGB_HD bool mul_in_range(uint64_t x, uint64_t y) {
+  const int ex = (int)((x >> 52) & 0x7FF), ey = (int)(y >> 52);
+  if ((x << 1) == 0) return ey != 0 && ey != 0x7FF;
+  return ex != 0 && ex != 0x7FF && ey != 0 && ey != 0x7FF && ex + ey - 1023 >= 1 && ex + ey - 1023 <= 2045;
 }
 
 // a + b for non-negative finite a, b (zero and subnormal included).  Fast

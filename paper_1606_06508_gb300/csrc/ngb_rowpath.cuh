@@ -109,82 +109,6 @@ __device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
   return __shfl_sync(FULL, q[0][0], 0);
 }
 
-// Forward, one warp per vector of length 5 <= n <= 32 V CH.  yr may be null
-// (norm only).  The whole warp must call it with the same arguments.
-template <typename T, int V, int CH>
-__device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
-                                             const VecOut<T>& out, int64_t vec) {
-  T v[CH][V];
-  MagTrack<T> mt;
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    const int k0 = 32 * V * c + V * lane;
-    if (k0 < n) {
-      Vec<T, V>::load(xr + k0, v[c]);
-    } else {
-#pragma unroll
-      for (int e = 0; e < V; ++e) v[c][e] = T(0);
-    }
-#pragma unroll
-    for (int e = 0; e < V; ++e) mt.take(v[c][e]);  // zero padding changes neither m nor the zero test
-  }
-  mt.warp_reduce();
-  if (mt.zero()) {  // every component compares equal to zero
-    if (yr) {
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int k0 = 32 * V * c + V * lane;
-        T z[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) z[e] = T(0);
-        if (k0 < n) Vec<T, V>::store(yr + k0, z);
-      }
-    }
-    if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
-    return;
-  }
-  if (mt.has_nan()) {
-    mt = MagTrack<T>();
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-#pragma unroll
-      for (int e = 0; e < V; ++e) mt.take_skip_nan(v[c][e]);
-    }
-    mt.warp_reduce();
-  }
-  const int code = mt.code();
-  const T cf = factor_of<T, true>(code);
-  if (code != CODE_ONE) {  // warp-uniform: no multiply when c = 1
-    const int E = Pow2Scale<T>::exponent(code);
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-#pragma unroll
-      for (int e = 0; e < V; ++e) v[c][e] = Pow2Scale<T>::apply(cf, E, v[c][e]);
-    }
-  }
-  T q[CH][V];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-#pragma unroll
-    for (int e = 0; e < V; ++e) q[c][e] = FP<T>::mul(v[c][e], v[c][e]);
-  }
-  const T rt = FP<T>::sqrt(warp_cr_tree<T, V, CH>(q, n, lane));
-  const T h = FP<T>::rcp(rt);
-  if (yr) {
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int k0 = 32 * V * c + V * lane;
-      if (k0 < n) {
-        T o[V];
-#pragma unroll
-        for (int e = 0; e < V; ++e) o[e] = FP<T>::mul(h, v[c][e]);
-        Vec<T, V>::store(yr + k0, o);
-      }
-    }
-  }
-  if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
-}
-
 // Backward, one warp per vector: dot = CR(y_k g_k), grad_k = ((g_k - y_k dot) h) c.
 template <typename T, int V, int CH>
 __device__ __forceinline__ void warp_backward(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
@@ -365,11 +289,8 @@ __device__ __forceinline__ void block_forward(const T* __restrict__ xr, T* yr, i
   const int code = mt.code();
   const T cf = factor_of<T, true>(code);
   T q[CH];
-#pragma unroll
-  for (int c = 0; c < CH; ++c) {
-    v[c] = scale_by(code, cf, v[c]);
-    q[c] = FP<T>::mul(v[c], v[c]);
-  }
+  if (code != CODE_ONE) Chunk<T, CH, false>::scale(cf, Pow2Scale<T>::exponent(code), v);
+  Chunk<T, CH, false>::squares(v, q);
   const T rt = FP<T>::sqrt(block_cr_tree<T, B, CH>(q, n, sh));
   const T h = FP<T>::rcp(rt);
   if (yr) {
@@ -404,22 +325,30 @@ __device__ __forceinline__ void block_forward_stream(const T* __restrict__ xr, T
   }
   const int code = mt.code();
   const T cf = factor_of<T, true>(code);
+  const int E = Pow2Scale<T>::exponent(code);
   T acc[G];
+  {
+    T a[G];
 #pragma unroll
-  for (int i = 0; i < G; ++i) {
-    const int k = B * i + t;
-    const T a = k < n ? scale_by(code, cf, xr[k]) : T(0);
-    acc[i] = FP<T>::mul(a, a);
+    for (int i = 0; i < G; ++i) {
+      const int k = B * i + t;
+      a[i] = k < n ? xr[k] : T(0);
+    }
+    if (code != CODE_ONE) Chunk<T, G, false>::scale(cf, E, a);
+    Chunk<T, G, false>::squares(a, acc);
   }
   for (int base = CR_SLOTS; base < n; base += CR_SLOTS) {
+    T a[G], q[G];
 #pragma unroll
     for (int i = 0; i < G; ++i) {
       const int k = base + B * i + t;
-      if (k < n) {
-        const T a = scale_by(code, cf, xr[k]);
-        acc[i] = FP<T>::add(acc[i], FP<T>::mul(a, a));
-      }
+      a[i] = k < n ? xr[k] : T(0);
     }
+    if (code != CODE_ONE) Chunk<T, G, false>::scale(cf, E, a);
+    Chunk<T, G, false>::squares(a, q);
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+      if (base + B * i + t < n) acc[i] = FP<T>::add(acc[i], q[i]);
   }
   const int used = n < CR_SLOTS ? n : CR_SLOTS;
 #pragma unroll
@@ -430,8 +359,13 @@ __device__ __forceinline__ void block_forward_stream(const T* __restrict__ xr, T
   }
   const T rt = FP<T>::sqrt(block_cr_finish<T, B>(acc[0], used, sh));
   const T h = FP<T>::rcp(rt);
-  if (yr)
-    for (int k = t; k < n; k += B) yr[k] = FP<T>::mul(h, scale_by(code, cf, xr[k]));
+  if (yr) {
+    for (int k = t; k < n; k += B) {
+      T a[1] = {xr[k]};
+      if (code != CODE_ONE) Chunk<T, 1, false>::scale(cf, E, a);
+      yr[k] = FP<T>::mul(h, a[0]);
+    }
+  }
   if (t == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }
 
@@ -546,7 +480,7 @@ __device__ __forceinline__ void stream_load8(const T* __restrict__ p, int base, 
 
 // Pass 2 of the forward: the scaled squares in the order CR(n).  SCALED
 // selects x~ = c x; otherwise x~ = x (c = 1).
-template <typename T, bool SCALED>
+template <typename T, bool SCALED, bool EMU>
 __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n, int lane, T cf, int E) {
   T acc[8];
 #pragma unroll
@@ -554,46 +488,42 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
   {  // first round: one term per slot (slots beyond n are never read by the tree)
     T v[8];
     stream_load8(xr, 0, n, lane, v);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
-      acc[i] = FP<T>::mul(t, t);
-    }
+    if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
+    Chunk<T, 8, EMU>::squares(v, acc);
   }
   int base = 256;
   for (; base + 256 <= n; base += 256) {  // full rounds
-    T v[8];
+    T v[8], q[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = xr[base + 32 * i + lane];
+    if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
+    Chunk<T, 8, EMU>::squares(v, q);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
-      acc[i] = FP<T>::add(acc[i], FP<T>::mul(t, t));
-    }
+    for (int i = 0; i < 8; ++i) acc[i] = FP<T>::add(acc[i], q[i]);
   }
   if (base < n) {  // last, partial round
-    T v[8];
+    T v[8], q[8];
     stream_load8(xr, base, n, lane, v);
+    if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
+    Chunk<T, 8, EMU>::squares(v, q);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const T t = SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i];
-      if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], FP<T>::mul(t, t));
-    }
+    for (int i = 0; i < 8; ++i)
+      if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q[i]);
   }
   return stream_tree<T>(acc, n, lane);
 }
 
 // Pass 3 of the forward: x^ = h x~, written with evict-first stores.
-template <typename T, bool SCALED>
+template <typename T, bool SCALED, bool EMU>
 __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
   int base = 0;
   for (; base + 256 <= n; base += 256) {
     T v[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __ldcs(xr + base + 32 * i + lane);
+    if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      __stcs(yr + base + 32 * i + lane, FP<T>::mul(h, SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i]));
+    for (int i = 0; i < 8; ++i) __stcs(yr + base + 32 * i + lane, Chunk<T, 8, EMU>::output(i, h, v[i]));
   }
   if (base < n) {
     T v[8];
@@ -602,20 +532,22 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
       const int k = base + 32 * i + lane;
       v[i] = k < n ? __ldcs(xr + k) : T(0);
     }
+    if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = base + 32 * i + lane;
-      if (k < n) __stcs(yr + k, FP<T>::mul(h, SCALED ? Pow2Scale<T>::apply(cf, E, v[i]) : v[i]));
+      if (k < n) __stcs(yr + k, Chunk<T, 8, EMU>::output(i, h, v[i]));
     }
   }
 }
 
-// Forward, one warp per vector of any length (5 <= n <= 2^20), three passes
-// over the vector: (1) largest magnitude and zero test, (2) scaled squares,
-// (3) outputs.  yr may be null (norm only).
+// Pass 1 of the streaming forward: the largest magnitude and the zero test.
+// For a zero vector it writes the zero result and returns CODE_ZERO;
+// otherwise it returns the factor code and sets `emu` when the integer-pipe
+// steps take every component (binary64).
 template <typename T>
-__device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
-                                                    const VecOut<T>& out, int64_t vec) {
+__device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int n, int lane, const VecOut<T>& out,
+                                            int64_t vec, bool& emu) {
   MagTrack<T> mt;
   for (int base = 0; base < n; base += 256) {
     T v[8];
@@ -628,7 +560,8 @@ __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T*
     if (yr)
       for (int k = lane; k < n; k += 32) __stcs(yr + k, T(0));
     if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
-    return;
+    emu = false;
+    return CODE_ZERO;
   }
   if (mt.has_nan()) {
     mt = MagTrack<T>();
@@ -636,17 +569,210 @@ __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T*
     mt.warp_reduce();
   }
   const int code = mt.code();
+  emu = mt.emu_ok(code);
+  return code;
+}
+
+// Pass 2 for a vector with factor code `code` (not CODE_ZERO).
+template <typename T>
+__device__ __forceinline__ T stream_pass2(const T* __restrict__ xr, int n, int lane, int code, bool emu) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  const bool scaled = code != CODE_ONE;
-  const T rt = FP<T>::sqrt(scaled ? stream_sum_squares<T, true>(xr, n, lane, cf, E)
-                                  : stream_sum_squares<T, false>(xr, n, lane, cf, E));
+  if (sizeof(T) == 8 && emu) {
+    return code != CODE_ONE ? stream_sum_squares<T, true, true>(xr, n, lane, cf, E)
+                            : stream_sum_squares<T, false, true>(xr, n, lane, cf, E);
+  }
+  return code != CODE_ONE ? stream_sum_squares<T, true, false>(xr, n, lane, cf, E)
+                          : stream_sum_squares<T, false, false>(xr, n, lane, cf, E);
+}
+
+// Pass 3: x^ = h x~.
+template <typename T>
+__device__ __forceinline__ void stream_pass3(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code,
+                                             bool emu) {
+  const T cf = factor_of<T, true>(code);
+  const int E = Pow2Scale<T>::exponent(code);
+  if (sizeof(T) == 8 && emu) {
+    if (code != CODE_ONE) stream_write<T, true, true>(xr, yr, n, lane, h, cf, E);
+    else stream_write<T, false, true>(xr, yr, n, lane, h, cf, E);
+  } else {
+    if (code != CODE_ONE) stream_write<T, true, false>(xr, yr, n, lane, h, cf, E);
+    else stream_write<T, false, false>(xr, yr, n, lane, h, cf, E);
+  }
+}
+
+// Passes 2 and 3 with the hardware operations, for any vector.
+template <typename T>
+__device__ __forceinline__ void warp_forward_stream_finish(const T* __restrict__ xr, T* yr, int n, int lane,
+                                                           const VecOut<T>& out, int64_t vec, int code) {
+  const T rt = FP<T>::sqrt(stream_pass2<T>(xr, n, lane, code, false));
+  const T h = FP<T>::rcp(rt);
+  if (yr) stream_pass3<T>(xr, yr, n, lane, h, code, false);
+  if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Forward, one warp per vector of any length (5 <= n <= 2^20), three passes
+// over the vector: (1) largest magnitude and zero test, (2) scaled squares,
+// (3) outputs.  yr may be null (norm only).
+template <typename T>
+__device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
+                                                    const VecOut<T>& out, int64_t vec) {
+  bool emu;
+  const int code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu);
+  if (code == CODE_ZERO) return;
+  const T rt = FP<T>::sqrt(stream_pass2<T>(xr, n, lane, code, emu));
+  const T h = FP<T>::rcp(rt);
+  if (yr) stream_pass3<T>(xr, yr, n, lane, h, code, emu);
+  if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+// Forward of nb <= NB vectors by one warp, streaming: passes 1 and 2 of every
+// vector, then one square root, one reciprocal and one norm product for the
+// whole batch (lane j holds vector j's sum of squares), then pass 3 of every
+// vector.  The binary64 square root and reciprocal take some twenty FP64
+// instructions that the whole warp issues for one value; the batch shares
+// them.  Same operations per vector as warp_forward_stream.  item(j, xr, yr,
+// n, vec) describes vector j; it is called again in the third phase rather
+// than keeping NB descriptors in registers.  Vectors longer than MAX_N are
+// done one by one on the spot: between passes 2 and 3 the batch's vectors
+// must stay in L1.  The loops over the batch are not unrolled: one copy of
+// each pass keeps the kernel small.
+template <typename T, int NB, int MAX_N, typename Item>
+__device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int nb, int lane, const VecOut<T>& out) {
+  T s = T(1);
+  int code_l = CODE_ONE;  // lane j < nb: the code of vector j
+  unsigned codes = 0;     // 2 bits per vector
+  unsigned emu_m = 0;
+#pragma unroll 1
+  for (int j = 0; j < NB; ++j) {
+    int code = CODE_ZERO;
+    if (j < nb) {
+      const T* xr;
+      T* yr;
+      int n;
+      int64_t vec;
+      item(j, xr, yr, n, vec);
+      bool emu;
+      if (MAX_N < MAX_LEN && n > MAX_N) {
+        warp_forward_stream<T>(xr, yr, n, lane, out, vec);
+        code = CODE_ZERO;  // done
+        emu = false;
+      } else {
+        code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu);
+      }
+      if (code != CODE_ZERO) {
+        const T sj = stream_pass2<T>(xr, n, lane, code, emu);
+        if (lane == j) {
+          s = sj;
+          code_l = code;
+        }
+        emu_m |= (emu ? 1u : 0u) << j;
+      }
+    }
+    codes |= (unsigned)code << (2 * j);
+  }
+  const T rt = FP<T>::sqrt(s);
+  const T h = FP<T>::rcp(rt);
+  const T r = FP<T>::mul(inverse_of<T, true>(code_l), rt);
+#pragma unroll 1
+  for (int j = 0; j < NB; ++j) {
+    const int code = (int)((codes >> (2 * j)) & 3u);
+    if (code != CODE_ZERO) {
+      const T* xr;
+      T* yr;
+      int n;
+      int64_t vec;
+      item(j, xr, yr, n, vec);
+      const T hj = __shfl_sync(FULL, h, j);
+      if (yr) stream_pass3<T>(xr, yr, n, lane, hj, code, (emu_m >> j) & 1u);
+      if (lane == j) out.put(vec, r, h, code);
+    }
+  }
+}
+
+// Steps 2-4 of the register-path forward: x~ = c x, the sum of squares in
+// the order CR(n), r~ = sqrt, h = 1/r~, x^ = h x~, r = sigma r~.
+template <typename T, int V, int CH, bool EMU>
+__device__ __forceinline__ void warp_forward_tail(T (&v)[CH][V], T* yr, int n, int lane, const VecOut<T>& out,
+                                                  int64_t vec, int code) {
+  const T cf = factor_of<T, true>(code);
+  T q[CH][V];
+  {
+    T (&vf)[CH * V] = reinterpret_cast<T (&)[CH * V]>(v);
+    if (code != CODE_ONE) Chunk<T, CH * V, EMU>::scale(cf, Pow2Scale<T>::exponent(code), vf);  // warp-uniform
+    Chunk<T, CH * V, EMU>::squares(vf, reinterpret_cast<T (&)[CH * V]>(q));
+  }
+  const T rt = FP<T>::sqrt(warp_cr_tree<T, V, CH>(q, n, lane));
   const T h = FP<T>::rcp(rt);
   if (yr) {
-    if (scaled) stream_write<T, true>(xr, yr, n, lane, h, cf, E);
-    else stream_write<T, false>(xr, yr, n, lane, h, cf, E);
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k0 = 32 * V * c + V * lane;
+      if (k0 < n) {
+        T o[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) o[e] = Chunk<T, CH * V, EMU>::output(c * V + e, h, v[c][e]);
+        Vec<T, V>::store(yr + k0, o);
+      }
+    }
   }
   if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
+}
+
+
+// Forward, one warp per vector of length 5 <= n <= 32 V CH.  yr may be null
+// (norm only).  The whole warp must call it with the same arguments.
+template <typename T, int V, int CH>
+__device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
+                                             const VecOut<T>& out, int64_t vec) {
+  T v[CH][V];
+  MagTrack<T> mt;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k0 = 32 * V * c + V * lane;
+    if (k0 < n) {
+      Vec<T, V>::load(xr + k0, v[c]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < V; ++e) v[c][e] = T(0);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) mt.take(v[c][e]);  // zero padding changes neither m nor the zero test
+  }
+  mt.warp_reduce();
+  if (mt.zero()) {  // every component compares equal to zero
+    if (yr) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int k0 = 32 * V * c + V * lane;
+        T z[V];
+#pragma unroll
+        for (int e = 0; e < V; ++e) z[e] = T(0);
+        if (k0 < n) Vec<T, V>::store(yr + k0, z);
+      }
+    }
+    if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
+    return;
+  }
+  if (mt.has_nan()) {
+    mt = MagTrack<T>();
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int e = 0; e < V; ++e) mt.take_skip_nan(v[c][e]);
+    }
+    mt.warp_reduce();
+  }
+  const int code = mt.code();
+  if (sizeof(T) == 8 && !mt.emu_ok(code)) {
+    // A binary64 vector with a component outside the range of the integer-pipe
+    // steps: the streaming passes (loops, so the compiler cannot turn this
+    // branch into predicated FP64 instructions on the common path) read it
+    // again from cache.  Same order CR(n), same results.
+    warp_forward_stream_finish<T>(xr, yr, n, lane, out, vec, code);
+    return;
+  }
+  warp_forward_tail<T, V, CH, sizeof(T) == 8>(v, yr, n, lane, out, vec, code);
 }
 
 // Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),

@@ -1,0 +1,121 @@
+// Host check of the integer-pipe binary64 square, product and sum (csrc/ngb_f64emu.cuh)
+// against the host's IEEE 754 binary64 multiply and add (round to nearest
+// even).  Prints "<cases> <in range> <mismatches>" per operation; any mismatch
+// on an operand the routine takes is a failure.  Built with -ffp-contract=off.
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "ngb_f64emu.cuh"
+
+static uint64_t sm_state;
+static uint64_t next64() {  // splitmix64
+  uint64_t z = (sm_state += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+static uint64_t bits(double x) { uint64_t b; std::memcpy(&b, &x, 8); return b; }
+static double val(uint64_t b) { double x; std::memcpy(&x, &b, 8); return x; }
+
+// a non-negative finite value with biased exponent e and a fraction that is
+// random, all ones, all zeros or has few bits set
+static uint64_t make(int e, int kind) {
+  uint64_t f = next64() & ngb::f64emu::FRAC;
+  if (kind == 1) f = ngb::f64emu::FRAC;
+  if (kind == 2) f = 0;
+  if (kind == 3) f &= next64() & next64() & next64();
+  if (kind == 4) f = ngb::f64emu::FRAC - (next64() & 0xFF);
+  if (kind == 5) f = (f & ~((uint64_t(1) << 27) - 1u)) | (uint64_t(1) << 26);  // m = 2^26 odd: square ties
+  return ((uint64_t)e << 52) | f;
+}
+
+int main(int argc, char** argv) {
+  const long n = argc > 1 ? atol(argv[1]) : 1000000;
+  sm_state = argc > 2 ? strtoull(argv[2], 0, 10) : 1;
+  long sq_fast = 0, sq_bad = 0, add_fast = 0, add_bad = 0;
+  for (long i = 0; i < n; ++i) {
+    const int kind = (int)(next64() % 6);
+    // exponents: uniform, or close to the edges of the fast path
+    int e;
+    const int sel = (int)(next64() % 4);
+    if (sel == 0) e = (int)(next64() % 2047);
+    else if (sel == 1) e = 509 + (int)(next64() % 6);   // squares near 2^-1022
+    else if (sel == 2) e = 1532 + (int)(next64() % 6);  // squares near 2^1024
+    else e = 1023 + (int)(next64() % 64) - 32;
+    const uint64_t a = make(e, kind);
+    bool ok = ngb::f64emu::square_in_range(a);
+    const uint64_t r = ngb::f64emu::square(a);
+    if (ok) {
+      ++sq_fast;
+      const double x = val(a);
+      if (r != bits(x * x)) {
+        if (sq_bad < 5) fprintf(stderr, "square %016llx: %016llx vs %016llx\n", (unsigned long long)a,
+                                (unsigned long long)r, (unsigned long long)bits(x * x));
+        ++sq_bad;
+      }
+    }
+    // sums: the second operand d binades below the first (d in [-2, 70]),
+    // or a subnormal, zero, or a value that makes a tie
+    const int eb = (int)(next64() % 2048) % 2046;
+    const int mode = (int)(next64() % 5);
+    uint64_t p = make(eb, kind), q;
+    if (mode == 0) {
+      int d = (int)(next64() % 73) - 2;
+      int es = eb - d;
+      if (es < 0) es = 0;
+      if (es > 2045) es = 2045;
+      q = make(es, (int)(next64() % 6));
+    } else if (mode == 1) {
+      q = next64() & ngb::f64emu::FRAC;  // subnormal or zero
+      if (next64() & 1) p = next64() & ngb::f64emu::FRAC;
+    } else if (mode == 2) {
+      q = 0;
+    } else if (mode == 3) {  // q = half an ulp of p (and neighbours): ties
+      int es = eb - 53;
+      if (es < 1) es = 1;
+      q = ((uint64_t)es << 52) | ((next64() % 3 == 0) ? 0 : (next64() & 1));
+    } else {
+      q = make(eb, (int)(next64() % 6));  // same binade: carry and normalisation
+    }
+    if (next64() & 1) { const uint64_t t = p; p = q; q = t; }
+    const uint64_t s = ngb::f64emu::add_nonneg(p, q, ok);
+    if (ok) {
+      ++add_fast;
+      const double ref = val(p) + val(q);
+      if (s != bits(ref)) {
+        if (add_bad < 5) fprintf(stderr, "add %016llx + %016llx: %016llx vs %016llx\n", (unsigned long long)p,
+                                 (unsigned long long)q, (unsigned long long)s, (unsigned long long)bits(ref));
+        ++add_bad;
+      }
+    }
+  }
+  long mul_fast = 0, mul_bad = 0;
+  for (long i = 0; i < n; ++i) {  // products: x of either sign, y > 0, exponents near the limits too
+    const int sel = (int)(next64() % 4);
+    int ex, ey;
+    if (sel == 0) { ex = 1 + (int)(next64() % 2045); ey = 1 + (int)(next64() % 2045); }
+    else if (sel == 1) { ex = 1 + (int)(next64() % 40); ey = 1023 - 40 + (int)(next64() % 80); }  // near 2^-1022
+    else if (sel == 2) { ex = 512 + (int)(next64() % 8); ey = 512 + (int)(next64() % 8); }
+    else { ex = 1023 + (int)(next64() % 64) - 32; ey = 1023 + (int)(next64() % 64) - 32; }
+    uint64_t x = make(ex, (int)(next64() % 6)), y = make(ey, (int)(next64() % 6));
+    if (next64() % 16 == 0) x = 0;
+    if (next64() & 1) x |= uint64_t(1) << 63;
+    if (ngb::f64emu::mul_in_range(x, y)) {
+      ++mul_fast;
+      const uint64_t r = ngb::f64emu::mul(x, y);
+      const double ref = val(x) * val(y);
+      if (r != bits(ref)) {
+        if (mul_bad < 5) fprintf(stderr, "mul %016llx * %016llx: %016llx vs %016llx\n", (unsigned long long)x,
+                                 (unsigned long long)y, (unsigned long long)r, (unsigned long long)bits(ref));
+        ++mul_bad;
+      }
+    }
+  }
+  printf("square %ld %ld %ld\n", n, sq_fast, sq_bad);
+  printf("mul %ld %ld %ld\n", n, mul_fast, mul_bad);
+  printf("add %ld %ld %ld\n", n, add_fast, add_bad);
+  return (sq_bad || add_bad || mul_bad) ? 1 : 0;
+}

@@ -1,4 +1,5 @@
-"""Helpers for the GPU parity tests: bitwise comparison with NaN as a class."""
+"""Helpers for the GPU parity tests: bitwise comparison with NaN as a class,
+and binary64 inputs at the limits of the integer-pipe steps."""
 import numpy as np
 import pytest
 
@@ -31,3 +32,30 @@ def cuda_device():
     import torch
     assert torch.cuda.is_available(), "GPU tests need a CUDA device"
     return torch.device("cuda:0")
+
+
+def f64_range_edges(count, dim, seed):
+    """binary64 vectors whose smallest nonzero component sits on, just below or
+    just above the lower limit of the integer-pipe scale and square (|c x| =
+    2^-511 after the factor c = 1, sigma_min = 2^592 or sigma_max = 2^-523),
+    next to vectors that stay inside it, with zeros, subnormals and the smallest
+    normal number mixed in."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((count, dim))
+    below = np.nextafter(2.0 ** -511, 0.0)
+    for i in range(count):
+        kind = i % 3
+        if kind == 0:      # c = 1: max near 1, limit 2^-511
+            edge = [2.0 ** -511, below, np.nextafter(2.0 ** -511, 1.0), 2.0 ** -600, 5e-324, 0.0]
+        elif kind == 1:    # sigma_max: max near 2^600, limit 2^12
+            x[i] *= 2.0 ** 600
+            edge = [2.0 ** 12, np.nextafter(2.0 ** 12, 0.0), 3.0 * 2.0 ** 11, 1.0, 2.0 ** -1022, 0.0]
+        else:              # sigma_min: max near 2^-500, subnormal components leave the integer path
+            x[i] *= 2.0 ** -500
+            edge = [2.0 ** -1022, np.nextafter(2.0 ** -1022, 0.0), 5e-324, 2.0 ** -700, 0.0, 2.0 ** -1000]
+        j = (i // 3) % (len(edge) + 1)
+        if j < len(edge):  # the last choice leaves the vector untouched
+            x[i, int(rng.integers(dim))] = edge[j]
+            if j % 2:
+                x[i, int(rng.integers(dim))] = -edge[j]
+    return x

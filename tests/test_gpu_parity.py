@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, cuda_device
+from gpu_util import assert_bits, cuda_device, f64_range_edges
 from paper_1606_06508_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -159,3 +159,10 @@ def test_rotation(dev, f):
     oR, orr = oracle.rotation(q)
     assert_bits(_np(R), oR, "rotation R")
     assert_bits(_np(r), orr, "rotation norm")
+
+
+@pytest.mark.parametrize("dim", [5, 9, 17, 40, 256, 1000, 1024, 1025, 3000, 20000])
+def test_f64_integer_pipe_limits(dev, dim):
+    count = max(36, min(1200, 300000 // dim))
+    x = f64_range_edges(count, dim, seed=dim)
+    _check_forward(dev, x, dim, what=f"f64 integer-pipe limits d={dim}")

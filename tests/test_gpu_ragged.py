@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, cuda_device
+from gpu_util import assert_bits, cuda_device, f64_range_edges
 from paper_1606_06508_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -175,3 +175,27 @@ def test_autotune(dev, f, tmp_path):
     assert plan2.autotune(offt, cache) == m  # read back from the cache
     y = api.normalize(xt, offt, plan=plan)
     assert_bits(_np(y), oracle.normalize(x, dim=0, offsets=off)[0], f"{f} autotuned")
+
+
+def test_ragged_f64_integer_pipe_limits(dev):
+    """Warp and block items of a ragged binary64 batch whose components sit at
+    the limits of the integer-pipe scale and square (see
+    gpu_util.f64_range_edges), under two mappings."""
+    from paper_1606_06508_gb300 import api
+    rng = np.random.default_rng(12)
+    lengths = rng.integers(17, 3000, size=600).astype(np.int64)
+    lengths[::50] = 9000
+    off = synth.offsets_from_lengths(lengths)
+    x = np.empty(int(off[-1]))
+    for i, n in enumerate(lengths):
+        x[off[i]:off[i + 1]] = f64_range_edges(3, int(n), seed=i)[i % 3]
+    oy, orr, oh, oc = oracle.normalize(x, dim=0, offsets=off)
+    xt, offt = _to(dev, x), _to(dev, off)
+    plan = api.Plan(len(lengths), xt.dtype)
+    for m in ((8, 8192, 256, 0), (8, 1024, 128, 0)):
+        plan.set_mapping(*m)
+        y, r, h, c = api.normalize(xt, offt, return_norm=True, save=True, plan=plan)
+        tag = f"f64 limits mapping={m}"
+        assert_bits(_np(y), oy, tag + " y")
+        assert_bits(_np(r), orr, tag + " norm")
+        assert_bits(_np(c), oc, tag + " code")
