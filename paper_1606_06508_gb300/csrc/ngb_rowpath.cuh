@@ -542,18 +542,53 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
 }
 
 // Pass 1 of the streaming forward: the largest magnitude and the zero test.
-// For a zero vector it writes the zero result and returns CODE_ZERO;
-// otherwise it returns the factor code and sets `emu` when the integer-pipe
-// steps take every component (binary64).
+// binary32 also runs pass 2 speculatively for the factor c = 1 (the sum of
+// squares of the unscaled components in the order CR(n)), which saves a pass
+// over the vector whenever no scaling is needed.  binary64 does not: there
+// the squares are integer-pipe work that would slow this first, HBM-bound
+// pass (measured: 15 % slower on the ragged binary64 workload).  For a zero
+// vector it writes the zero result and returns CODE_ZERO.  Otherwise it
+// returns the factor code and sets `emu` when the integer-pipe steps take
+// every component; `s` is the algorithm's sum of squares when `have_s`.  When
+// the speculation fails (another factor) the caller runs pass 2 and the
+// speculative sum, possibly overflowed, is discarded unread.
 template <typename T>
 __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int n, int lane, const VecOut<T>& out,
-                                            int64_t vec, bool& emu) {
+                                            int64_t vec, bool& emu, T& s, bool& have_s) {
+  constexpr bool SPEC = sizeof(T) == 4;
   MagTrack<T> mt;
-  for (int base = 0; base < n; base += 256) {
+  T acc[8];
+  {
     T v[8];
-    stream_load8(xr, base, n, lane, v);
+    stream_load8(xr, 0, n, lane, v);
 #pragma unroll
     for (int i = 0; i < 8; ++i) mt.take(v[i]);  // zero padding changes neither m nor the zero test
+    if (SPEC) Chunk<T, 8, false>::squares(v, acc);
+  }
+  int base = 256;
+  for (; base + 256 <= n; base += 256) {
+    T v[8], q[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = xr[base + 32 * i + lane];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mt.take(v[i]);
+    if (SPEC) {
+      Chunk<T, 8, false>::squares(v, q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) acc[i] = FP<T>::add(acc[i], q[i]);
+    }
+  }
+  if (base < n) {
+    T v[8], q[8];
+    stream_load8(xr, base, n, lane, v);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) mt.take(v[i]);
+    if (SPEC) {
+      Chunk<T, 8, false>::squares(v, q);
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q[i]);
+    }
   }
   mt.warp_reduce();
   if (mt.zero()) {
@@ -561,6 +596,7 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
       for (int k = lane; k < n; k += 32) __stcs(yr + k, T(0));
     if (lane == 0) out.put(vec, T(0), T(0), CODE_ZERO);
     emu = false;
+    have_s = false;
     return CODE_ZERO;
   }
   if (mt.has_nan()) {
@@ -570,44 +606,66 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
   }
   const int code = mt.code();
   emu = mt.emu_ok(code);
+  have_s = SPEC && code == CODE_ONE;
+  s = SPEC ? stream_tree<T>(acc, n, lane) : T(0);
   return code;
 }
 
-// Pass 2 for a vector with factor code `code` (not CODE_ZERO).
-template <typename T>
-__device__ __forceinline__ T stream_pass2(const T* __restrict__ xr, int n, int lane, int code, bool emu) {
+// Pass 2 for a vector with factor code `code` (not CODE_ZERO); EMU selects
+// the binary64 integer-pipe steps.
+template <typename T, bool EMU>
+__device__ __forceinline__ T stream_pass2(const T* __restrict__ xr, int n, int lane, int code) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  if (sizeof(T) == 8 && emu) {
-    return code != CODE_ONE ? stream_sum_squares<T, true, true>(xr, n, lane, cf, E)
-                            : stream_sum_squares<T, false, true>(xr, n, lane, cf, E);
-  }
-  return code != CODE_ONE ? stream_sum_squares<T, true, false>(xr, n, lane, cf, E)
-                          : stream_sum_squares<T, false, false>(xr, n, lane, cf, E);
+  return code != CODE_ONE ? stream_sum_squares<T, true, EMU>(xr, n, lane, cf, E)
+                          : stream_sum_squares<T, false, EMU>(xr, n, lane, cf, E);
 }
 
 // Pass 3: x^ = h x~.
-template <typename T>
-__device__ __forceinline__ void stream_pass3(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code,
-                                             bool emu) {
+template <typename T, bool EMU>
+__device__ __forceinline__ void stream_pass3(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  if (sizeof(T) == 8 && emu) {
-    if (code != CODE_ONE) stream_write<T, true, true>(xr, yr, n, lane, h, cf, E);
-    else stream_write<T, false, true>(xr, yr, n, lane, h, cf, E);
-  } else {
-    if (code != CODE_ONE) stream_write<T, true, false>(xr, yr, n, lane, h, cf, E);
-    else stream_write<T, false, false>(xr, yr, n, lane, h, cf, E);
-  }
+  if (code != CODE_ONE) stream_write<T, true, EMU>(xr, yr, n, lane, h, cf, E);
+  else stream_write<T, false, EMU>(xr, yr, n, lane, h, cf, E);
+}
+
+// The hardware-operation passes of a binary64 vector that the integer-pipe
+// steps do not take (rare: components 2^511 times smaller than the largest,
+// subnormals with sigma_min, infinities, NaN).  Out of line, so that the
+// common path of the kernels stays small in the instruction cache.
+template <typename T>
+__device__ __noinline__ T stream_pass2_slow(const T* __restrict__ xr, int n, int lane, int code) {
+  return stream_pass2<T, false>(xr, n, lane, code);
+}
+template <typename T>
+__device__ __noinline__ void stream_pass3_slow(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code) {
+  stream_pass3<T, false>(xr, yr, n, lane, h, code);
+}
+
+// Pass 2 and pass 3 of either kind: binary32 always uses the hardware
+// operations inline; binary64 the integer-pipe steps inline when `emu`, the
+// out-of-line hardware passes otherwise.
+template <typename T>
+__device__ __forceinline__ T stream_pass2_any(const T* __restrict__ xr, int n, int lane, int code, bool emu) {
+  if (sizeof(T) == 4) return stream_pass2<T, false>(xr, n, lane, code);
+  return emu ? stream_pass2<T, true>(xr, n, lane, code) : stream_pass2_slow<T>(xr, n, lane, code);
+}
+template <typename T>
+__device__ __forceinline__ void stream_pass3_any(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code,
+                                                 bool emu) {
+  if (sizeof(T) == 4) stream_pass3<T, false>(xr, yr, n, lane, h, code);
+  else if (emu) stream_pass3<T, true>(xr, yr, n, lane, h, code);
+  else stream_pass3_slow<T>(xr, yr, n, lane, h, code);
 }
 
 // Passes 2 and 3 with the hardware operations, for any vector.
 template <typename T>
 __device__ __forceinline__ void warp_forward_stream_finish(const T* __restrict__ xr, T* yr, int n, int lane,
                                                            const VecOut<T>& out, int64_t vec, int code) {
-  const T rt = FP<T>::sqrt(stream_pass2<T>(xr, n, lane, code, false));
+  const T rt = FP<T>::sqrt(stream_pass2_any<T>(xr, n, lane, code, false));
   const T h = FP<T>::rcp(rt);
-  if (yr) stream_pass3<T>(xr, yr, n, lane, h, code, false);
+  if (yr) stream_pass3_any<T>(xr, yr, n, lane, h, code, false);
   if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }
 
@@ -617,12 +675,14 @@ __device__ __forceinline__ void warp_forward_stream_finish(const T* __restrict__
 template <typename T>
 __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
                                                     const VecOut<T>& out, int64_t vec) {
-  bool emu;
-  const int code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu);
+  bool emu, have_s;
+  T s;
+  const int code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, s, have_s);
   if (code == CODE_ZERO) return;
-  const T rt = FP<T>::sqrt(stream_pass2<T>(xr, n, lane, code, emu));
+  if (!have_s) s = stream_pass2_any<T>(xr, n, lane, code, emu);
+  const T rt = FP<T>::sqrt(s);
   const T h = FP<T>::rcp(rt);
-  if (yr) stream_pass3<T>(xr, yr, n, lane, h, code, emu);
+  if (yr) stream_pass3_any<T>(xr, yr, n, lane, h, code, emu);
   if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }
 
@@ -652,16 +712,17 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
       int n;
       int64_t vec;
       item(j, xr, yr, n, vec);
-      bool emu;
+      bool emu, have_s;
+      T sj;
       if (MAX_N < MAX_LEN && n > MAX_N) {
         warp_forward_stream<T>(xr, yr, n, lane, out, vec);
         code = CODE_ZERO;  // done
         emu = false;
       } else {
-        code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu);
+        code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, sj, have_s);
       }
       if (code != CODE_ZERO) {
-        const T sj = stream_pass2<T>(xr, n, lane, code, emu);
+        if (!have_s) sj = stream_pass2_any<T>(xr, n, lane, code, emu);
         if (lane == j) {
           s = sj;
           code_l = code;
@@ -684,7 +745,7 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
       int64_t vec;
       item(j, xr, yr, n, vec);
       const T hj = __shfl_sync(FULL, h, j);
-      if (yr) stream_pass3<T>(xr, yr, n, lane, hj, code, (emu_m >> j) & 1u);
+      if (yr) stream_pass3_any<T>(xr, yr, n, lane, hj, code, (emu_m >> j) & 1u);
       if (lane == j) out.put(vec, r, h, code);
     }
   }
