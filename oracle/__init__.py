@@ -23,6 +23,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "normalize_oracle.c")
 HDR = os.path.join(HERE, "oracle_impl.h")
 LIB = os.path.join(HERE, "liboracle.so")
+# A prebuilt oracle library to load instead (the mutation test of the pins
+# points this at deliberately broken copies); never built here.
+LIB_OVERRIDE = os.environ.get("NGB_ORACLE_LIB")
 
 CODE_ONE, CODE_SMIN, CODE_SMAX, CODE_ZERO = 0, 1, 2, 3
 VECTOR_SEMANTICS = 1
@@ -38,6 +41,8 @@ _lock = threading.Lock()
 
 def build(force: bool = False) -> str:
     """Compile the oracle library if it is missing or older than its sources."""
+    if LIB_OVERRIDE:
+        return LIB_OVERRIDE
     stale = (not os.path.exists(LIB) or
              os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
     if force or stale:
@@ -51,8 +56,7 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(LIB)
+            lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
             for sfx in ("f32", "f64"):
                 f = getattr(lib, f"oracle_normalize_{sfx}")
