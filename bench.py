@@ -262,11 +262,45 @@ def parity_ragged(x, off_t, y, k=2048, grad=None, g=None):
 # ---------------------------------------------------------------------------- workloads
 class Work:
     """One workload: a step (device-resident inputs), its units and algorithmic
-    bytes, the dominant kernel, host buffers for the end-to-end figure."""
+    bytes, the dominant kernel, host buffers for the end-to-end figure, and
+    for binary64 the algorithmic FP64 operations per step."""
 
     def __init__(self, **kw):
         self.flush = False
+        self.dp_ops = None
         self.__dict__.update(kw)
+
+
+DP_OPS_MODEL = ("binary64 operations of the paper's sequence done on the FP64 pipe: 3 per element (square, "
+                "sum, output product) + 3 per vector (square root, reciprocal, norm product); backward 5 per "
+                "element (product, sum, product, difference, product); exact power-of-two scalings not counted")
+
+
+def fp64_rate(torch, L):
+    """Measured binary64 multiply + add rate of this GPU (FP64 operations per
+    second): ngb_fp64_probe, one wave of 8 blocks per SM, median of 5 timed launches."""
+    import ctypes
+    blocks = 8 * torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    out = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    ops = ctypes.c_int64(0)
+    s = torch.cuda.current_stream()
+
+    def fn():
+        L.check(L.ngb_fp64_probe(out.data_ptr(), blocks, 4096, ctypes.byref(ops), s.cuda_stream), "fp64 probe")
+    fn()
+    torch.cuda.synchronize()
+    t = statistics.median(time_events(fn, 5, s)) * 1e-3
+    return ops.value / t
+
+
+def dp_roofline(w, ms_per_step, rate):
+    """FP64-pipe bound of a binary64 step next to its byte bound."""
+    if w.dp_ops is None or not rate:
+        return None
+    bound_ms = w.dp_ops / rate * 1e3
+    return {"dp_ops_per_step": w.dp_ops, "fp64_ops_per_s": rate, "bound_ms": bound_ms,
+            "measured_ms": ms_per_step, "frac": bound_ms / ms_per_step, "ops_model": DP_OPS_MODEL,
+            "peak_source": "measured live: ngb_fp64_probe (dmul + dadd chains)"}
 
 
 def build_work(name, count, rank, torch, L, api, synth):
@@ -322,7 +356,8 @@ def build_work(name, count, rank, torch, L, api, synth):
                     units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
                     kernel=('k_rows_warp<float,4,2>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
                     step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 256, k=2048),
-                    bytes_model="2 x 256 x s per row")
+                    bytes_model="2 x 256 x s per row",
+                    dp_ops=(3 * rows * 256 + 3 * rows) if dt == torch.float64 else None)
 
     if name in ("ragged_f32", "ragged_f64", "fwdbwd_ragged_f64"):
         dt = torch.float64 if "f64" in name else torch.float32
@@ -346,7 +381,8 @@ def build_work(name, count, rank, torch, L, api, synth):
                         units=cnt, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1), dtype=name[-3:],
                         kernel="k_classify + k_ragged (persistent)", launches=2, step=step, h2d=[x, off], d2h=[y],
                         parity=lambda: parity_ragged(x, off, y), mapping=list(mapping), plan=plan,
-                        bytes_model="2 n s per vector + 8 B offsets")
+                        bytes_model="2 n s per vector + 8 B offsets",
+                        dp_ops=(3 * x.numel() + 3 * cnt) if dt == torch.float64 else None)
         g = synth.normal_like_torch(x.shape, dt, seed=41 + seed, device=dev)
         gr = torch.empty_like(x)
         h = torch.empty(cnt, dtype=dt, device=dev)
@@ -362,7 +398,8 @@ def build_work(name, count, rank, torch, L, api, synth):
                     kernel="k_classify + k_ragged; k_classify + k_ragged_bwd_{blocks,warps,threads}", launches=6,
                     step=step, h2d=[x, g, off], d2h=[gr], parity=lambda: parity_ragged(x, off, y, grad=gr, g=g),
                     mapping=list(mapping), plan=plan,
-                    bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector")
+                    bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector",
+                    dp_ops=8 * x.numel() + 3 * cnt)
 
     if name == "vec3_f64":
         xh = synth.vectors3_f64(65536, seed=0 + seed)
@@ -376,7 +413,7 @@ def build_work(name, count, rank, torch, L, api, synth):
         return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
                     units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_staged<double,3>", launches=1,
                     step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 3, k=cnt), flush=True,
-                    bytes_model="24 B read + 24 B written per vector")
+                    bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
     raise ValueError(f"unknown workload {name}")
 
 
@@ -384,7 +421,7 @@ WORKLOAD_NAMES = ["quat", "fwdbwd_quat", "rows_f32", "rows_f64", "ragged_f32", "
                   "vec3_f64"]
 
 
-def extras(torch, L, api, synth, peak):
+def extras(torch, L, api, synth, peak, rate):
     """Secondary measurements on this GPU (each step repeated 10 times,
     CUDA events): the other workloads, the copy ceiling, the naive algorithm."""
     out = {}
@@ -402,6 +439,9 @@ def extras(torch, L, api, synth, peak):
             out[name] = {"vectors_per_s": w.units / t, "ms": t * 1e3, "GB_per_s": w.bytes / t / 1e9,
                          "frac_of_hbm_peak": w.bytes / t / 1e9 / peak, "algorithmic_bytes": w.bytes,
                          "kernel": w.kernel, **({"mapping": w.mapping} if hasattr(w, "mapping") else {})}
+            dp = dp_roofline(w, t * 1e3, rate)
+            if dp:
+                out[name]["dp_roofline"] = dp
             del w
         except Exception as e:  # report, do not hide
             out[name] = {"error": repr(e)}
@@ -541,6 +581,11 @@ def run_ours(args):
             "gpu_launches": args.steps * w.launches,
             "clocks": clocks,
         }
+        rate = fp64_rate(torch, L)
+        result["fp64_ops_per_s"] = rate
+        dp = dp_roofline(w, ms / args.steps, rate)
+        if dp:
+            result["dp_roofline"] = dp
     # e2e through pinned host buffers: H2D of the step's inputs, the call, D2H of its result
     e2e_steps = max(1, min(args.steps, 20))
     hin = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in w.h2d]
@@ -580,7 +625,7 @@ def run_ours(args):
                 del hin, hout
                 w = None
                 torch.cuda.empty_cache()
-                result["also"] = extras(torch, L, api, synth, peak)
+                result["also"] = extras(torch, L, api, synth, peak, rate)
             result["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(result), flush=True)
     if world > 1:

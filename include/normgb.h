@@ -175,6 +175,15 @@ ngb_status ngb_copy(void* dst, const void* src, int64_t bytes, ngb_stream_t stre
 ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream);
 ngb_status naive_normalize_f64(const double* x, double* y, int64_t count, int32_t dim, ngb_stream_t stream);
 
+/* Measurement aid (not the method): the binary64 pipe's throughput.  Launches
+ * `blocks` blocks of 256 threads; each thread runs 4 independent chains of
+ * `iters` steps a <- RN(RN(a * b) + c), two FP64 instructions per step, and
+ * writes one double to out[blocks * 256] (device memory owned by the caller).
+ * *fp64_ops (host, nullable) receives the number of FP64 operations issued;
+ * the caller times the launch on `stream`.  Errors: NGB_ERR_INVALID_ARG for a
+ * null out or non-positive sizes, NGB_ERR_CUDA for a launch failure. */
+ngb_status ngb_fp64_probe(double* out, int32_t blocks, int32_t iters, int64_t* fp64_ops, ngb_stream_t stream);
+
 /* Largest batch accepted by normalize_ragged_f32_noalloc. */
 #define NGB_NOALLOC_MAX_COUNT 262144
 

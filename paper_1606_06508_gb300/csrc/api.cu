@@ -435,6 +435,14 @@ ngb_status ngb_copy(void* dst, const void* src, int64_t bytes, ngb_stream_t stre
   return e == cudaSuccess ? NGB_OK : cuda_fail(e, "copy launch");
 }
 
+ngb_status ngb_fp64_probe(double* out, int32_t blocks, int32_t iters, int64_t* fp64_ops, ngb_stream_t stream) {
+  g_last_error.clear();
+  if (!out || blocks <= 0 || iters <= 0) return fail(NGB_ERR_INVALID_ARG, "out is required; blocks and iters > 0");
+  if (fp64_ops) *fp64_ops = (int64_t)blocks * 256 * 4 * 2 * (int64_t)iters;
+  cudaError_t e = ngb::launch_fp64_probe(out, blocks, iters, cs(stream));
+  return e == cudaSuccess ? NGB_OK : cuda_fail(e, "fp64 probe launch");
+}
+
 ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream) {
   g_last_error.clear();
   if (count < 0 || dim < 2 || dim > 4) return fail(NGB_ERR_INVALID_ARG, "count < 0 or dim not in 2..4");

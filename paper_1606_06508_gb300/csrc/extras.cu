@@ -177,4 +177,30 @@ cudaError_t launch_naive(const T* x, T* y, int64_t count, int dim, cudaStream_t 
 template cudaError_t launch_naive<float>(const float*, float*, int64_t, int, cudaStream_t);
 template cudaError_t launch_naive<double>(const double*, double*, int64_t, int, cudaStream_t);
 
+// Binary64 multiply-add throughput probe: every thread runs FP64_PROBE_CHAINS
+// independent chains a <- RN(RN(a * b) + c), `iters` steps each (two FP64
+// instructions per step), and writes its results so nothing is removed.
+constexpr int FP64_PROBE_CHAINS = 4;
+constexpr int FP64_PROBE_THREADS = 256;
+
+__global__ void __launch_bounds__(FP64_PROBE_THREADS) k_fp64_probe(double* out, int iters) {
+  double a[FP64_PROBE_CHAINS];
+  const double b = 1.0 + 0x1p-30 * (threadIdx.x & 7), c = 0x1p-40;
+#pragma unroll
+  for (int j = 0; j < FP64_PROBE_CHAINS; ++j) a[j] = 1.0 + j * 0x1p-20;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int j = 0; j < FP64_PROBE_CHAINS; ++j) a[j] = __dadd_rn(__dmul_rn(a[j], b), c);
+  }
+  double r = 0.0;
+#pragma unroll
+  for (int j = 0; j < FP64_PROBE_CHAINS; ++j) r = __dadd_rn(r, a[j]);
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s) {
+  k_fp64_probe<<<blocks, FP64_PROBE_THREADS, 0, s>>>(out, iters);
+  return cudaGetLastError();
+}
+
 }  // namespace ngb

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(B) k_ragged_bwd_blocks(RaggedArgs<T> a) {
 
 // Backward, warp list: one warp per vector, warp-stride over the list.
 template <typename T>
-__global__ void __launch_bounds__(256) k_ragged_bwd_warps(RaggedArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_ragged_bwd_warps(RaggedArgs<T> a) {
   const int lane = threadIdx.x & 31;
   const int nwarp = a.sc.counts[1];
   const int32_t* Lw = a.sc.items + a.count;

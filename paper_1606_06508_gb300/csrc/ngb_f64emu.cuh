@@ -124,6 +124,16 @@ NGB_HD uint64_t mul(uint64_t x, uint64_t y) {
   return ex == 0 ? (x & 0x8000000000000000ull) : (((uint64_t)rhi << 32) | sig_lo);
 }
 
+// x * y for x, y of either sign: the product of |x| and |y| by mul() with the
+// sign x_s XOR y_s; a zero operand gives the signed zero.  Valid when x and
+// y are zero or normal with a normal product (mul_in_range on |x|, |y|).
+NGB_HD uint64_t mul_signed(uint64_t x, uint64_t y) {
+  const uint64_t SIGN = 0x8000000000000000ull;
+  const uint64_t s = (x ^ y) & SIGN;
+  if ((x << 1) == 0 || (y << 1) == 0) return s;
+  return mul(x & ~SIGN, y & ~SIGN) | s;
+}
+
 // The operands mul() takes (y > 0): x = +-0, or x and y normal with a normal
 // product: the biased exponent ex + ey - 1023 (+1) of x y within [1, 2046].
 NGB_HD bool mul_in_range(uint64_t x, uint64_t y) {

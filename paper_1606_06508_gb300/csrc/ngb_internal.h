@@ -52,6 +52,7 @@ int ragged_full_wave(const RaggedMapping& map, bool backward);
 
 // Measurement aids and extra entry points.
 cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
+cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
 template <typename T>
 cudaError_t launch_naive(const T* x, T* y, int64_t count, int dim, cudaStream_t s);
 template <typename T>

@@ -836,16 +836,12 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
   warp_forward_tail<T, V, CH, sizeof(T) == 8>(v, yr, n, lane, out, vec, code);
 }
 
-// Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),
-// (2) grad_k = ((g_k - y_k dot) h) c.
-template <typename T>
-__device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr,
-                                                     int n, int lane, T h, int code) {
-  if (code == CODE_ZERO) {
-    for (int k = lane; k < n; k += 32) __stcs(gradr + k, T(0));
-    return;
-  }
-  const T cf = factor_of<T, true>(code);
+// Backward pass 1 (dot = CR(y_k g_k)), streaming.  EMU (binary64): the
+// products by f64emu::mul_signed, while `ry`, `rg` collect the integer keys of
+// y and g that decide afterwards whether every product was in its range.
+template <typename T, bool EMU>
+__device__ __forceinline__ T bwd_dot_pass(const T* __restrict__ yr, const T* __restrict__ gr, int n, int lane,
+                                          MagTrack<T>* ry, MagTrack<T>* rg) {
   T acc[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i) acc[i] = T(0);
@@ -855,12 +851,33 @@ __device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, c
     stream_load8(gr, base, n, lane, b);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const T q = FP<T>::mul(a[i], b[i]);
+      T q;
+      if constexpr (EMU) {
+        ry->take(a[i]);
+        rg->take(b[i]);
+        q = __longlong_as_double(static_cast<long long>(f64emu::mul_signed(
+            static_cast<uint64_t>(__double_as_longlong(a[i])), static_cast<uint64_t>(__double_as_longlong(b[i])))));
+      } else {
+        q = FP<T>::mul(a[i], b[i]);
+      }
       if (base == 0) acc[i] = q;
       else if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q);
     }
   }
-  const T dot = stream_tree<T>(acc, n, lane);
+  return stream_tree<T>(acc, n, lane);
+}
+
+template <typename T>
+__device__ __noinline__ T bwd_dot_pass_slow(const T* __restrict__ yr, const T* __restrict__ gr, int n, int lane) {
+  return bwd_dot_pass<T, false>(yr, gr, n, lane, nullptr, nullptr);
+}
+
+// Backward pass 2: grad_k = ((g_k - y_k dot) h) c.  SCALED = false skips the
+// multiplication by c = 1 (exact, so the same bits).  EMU: y_k dot by
+// f64emu::mul_signed.
+template <typename T, bool SCALED, bool EMU>
+__device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
+                                              int lane, T dot, T h, T cf) {
   for (int base = 0; base < n; base += 256) {
     T a[8], b[8];
 #pragma unroll
@@ -872,8 +889,65 @@ __device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, c
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = base + 32 * i + lane;
-      if (k < n) __stcs(gradr + k, FP<T>::mul(FP<T>::mul(FP<T>::sub(b[i], FP<T>::mul(a[i], dot)), h), cf));
+      T p;
+      if constexpr (EMU)
+        p = __longlong_as_double(static_cast<long long>(f64emu::mul_signed(
+            static_cast<uint64_t>(__double_as_longlong(a[i])), static_cast<uint64_t>(__double_as_longlong(dot)))));
+      else
+        p = FP<T>::mul(a[i], dot);
+      T o = FP<T>::mul(FP<T>::sub(b[i], p), h);
+      if (SCALED) o = FP<T>::mul(o, cf);
+      if (k < n) __stcs(gradr + k, o);
     }
+  }
+}
+
+// Whether f64emu::mul_signed takes every product a_k b_k, from the keys of
+// the a_k and of the b_k (MagTrack<double>: largest key, smallest nonzero
+// key): true when either side is all zero, or both are finite and normal
+// with 1 <= e_a + e_b - 1023 and e_a + e_b - 1023 <= 2045 for the extreme
+// biased exponents.
+__device__ __forceinline__ bool products_in_range(const MagTrack<double>& ta, const MagTrack<double>& tb) {
+  if (ta.k == 0u || tb.k == 0u) return true;
+  const uint32_t na = ta.kmin1 + 1u, nb = tb.kmin1 + 1u;  // smallest nonzero keys
+  if (ta.k >= MagTrack<double>::HI_INF || tb.k >= MagTrack<double>::HI_INF) return false;
+  if (na < (1u << 20) || nb < (1u << 20)) return false;  // a subnormal operand
+  const int emin = (int)(na >> 20) + (int)(nb >> 20) - 1023, emax = (int)(ta.k >> 20) + (int)(tb.k >> 20) - 1023;
+  return emin >= 1 && emax <= 2045;
+}
+
+// Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),
+// (2) grad_k = ((g_k - y_k dot) h) c.  binary64 forms the products on the
+// integer pipes when every one of them is in range (pass 1 runs that way
+// speculatively and runs again with the hardware products otherwise).
+template <typename T>
+__device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr,
+                                                     int n, int lane, T h, int code) {
+  if (code == CODE_ZERO) {
+    for (int k = lane; k < n; k += 32) __stcs(gradr + k, T(0));
+    return;
+  }
+  const T cf = factor_of<T, true>(code);
+  if constexpr (sizeof(T) == 8) {
+    MagTrack<T> ry, rg;
+    T dot = bwd_dot_pass<T, true>(yr, gr, n, lane, &ry, &rg);
+    ry.warp_reduce();
+    rg.warp_reduce();
+    if (!products_in_range(ry, rg)) dot = bwd_dot_pass_slow<T>(yr, gr, n, lane);
+    MagTrack<T> rd;
+    rd.take(dot);
+    const bool emu = products_in_range(ry, rd);
+    if (emu) {
+      if (code != CODE_ONE) bwd_grad_pass<T, true, true>(yr, gr, gradr, n, lane, dot, h, cf);
+      else bwd_grad_pass<T, false, true>(yr, gr, gradr, n, lane, dot, h, cf);
+    } else {
+      if (code != CODE_ONE) bwd_grad_pass<T, true, false>(yr, gr, gradr, n, lane, dot, h, cf);
+      else bwd_grad_pass<T, false, false>(yr, gr, gradr, n, lane, dot, h, cf);
+    }
+  } else {
+    const T dot = bwd_dot_pass<T, false>(yr, gr, n, lane, nullptr, nullptr);
+    if (code != CODE_ONE) bwd_grad_pass<T, true, false>(yr, gr, gradr, n, lane, dot, h, cf);
+    else bwd_grad_pass<T, false, false>(yr, gr, gradr, n, lane, dot, h, cf);
   }
 }
 

@@ -114,8 +114,31 @@ int main(int argc, char** argv) {
       }
     }
   }
+  long smul_fast = 0, smul_bad = 0;
+  for (long i = 0; i < n; ++i) {  // signed products, zeros of either sign included
+    int ex = 1023 + (int)(next64() % 200) - 100, ey = 1023 + (int)(next64() % 200) - 100;
+    if (next64() % 8 == 0) { ex = 1 + (int)(next64() % 30); ey = 1023 - 30 + (int)(next64() % 60); }
+    uint64_t x = make(ex, (int)(next64() % 6)), y = make(ey, (int)(next64() % 6));
+    if (next64() % 16 == 0) x = 0;
+    if (next64() % 16 == 0) y = 0;
+    if (next64() & 1) x |= uint64_t(1) << 63;
+    if (next64() & 1) y |= uint64_t(1) << 63;
+    const uint64_t ax = x & ~(uint64_t(1) << 63), ay = y & ~(uint64_t(1) << 63);
+    const bool zero = (ax == 0) || (ay == 0);
+    if (zero || (ngb::f64emu::mul_in_range(ax, ay) && ((ay >> 52) != 0))) {
+      ++smul_fast;
+      const uint64_t r = ngb::f64emu::mul_signed(x, y);
+      const double ref = val(x) * val(y);
+      if (r != bits(ref)) {
+        if (smul_bad < 5) fprintf(stderr, "mul_signed %016llx * %016llx: %016llx vs %016llx\n", (unsigned long long)x,
+                                  (unsigned long long)y, (unsigned long long)r, (unsigned long long)bits(ref));
+        ++smul_bad;
+      }
+    }
+  }
   printf("square %ld %ld %ld\n", n, sq_fast, sq_bad);
+  printf("mul_signed %ld %ld %ld\n", n, smul_fast, smul_bad);
   printf("mul %ld %ld %ld\n", n, mul_fast, mul_bad);
   printf("add %ld %ld %ld\n", n, add_fast, add_bad);
-  return (sq_bad || add_bad || mul_bad) ? 1 : 0;
+  return (sq_bad || add_bad || mul_bad || smul_bad) ? 1 : 0;
 }

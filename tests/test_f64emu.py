@@ -32,5 +32,7 @@ def test_square_and_sum_match_ieee(checker, seed):
     assert bad == 0 and taken > cases // 3
     cases, taken, bad = rows["mul"]
     assert bad == 0 and taken > cases // 2
+    cases, taken, bad = rows["mul_signed"]
+    assert bad == 0 and taken > cases // 2
     cases, taken, bad = rows["add"]
     assert bad == 0 and taken > cases // 2
