@@ -517,6 +517,23 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
 template <typename T, bool SCALED, bool EMU>
 __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
   int base = 0;
+  if (sizeof(T) == 4) {  // binary32: two rounds of loads in flight
+    for (; base + 512 <= n; base += 512) {
+      T v[2][8];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[r][i] = __ldcs(xr + base + 256 * r + 32 * i + lane);
+      }
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v[r]);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          __stcs(yr + base + 256 * r + 32 * i + lane, Chunk<T, 8, EMU>::output(i, h, v[r][i]));
+      }
+    }
+  }
   for (; base + 256 <= n; base += 256) {
     T v[8];
 #pragma unroll
@@ -566,6 +583,28 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
     if (SPEC) Chunk<T, 8, false>::squares(v, acc);
   }
   int base = 256;
+  // binary32: two rounds (16 loads per lane) in flight per iteration, taken
+  // in ascending order, so the slot sums are unchanged
+  constexpr int R = sizeof(T) == 4 ? 2 : 1;
+  for (; base + 256 * R <= n; base += 256 * R) {
+    T v[R][8];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[r][i] = xr[base + 256 * r + 32 * i + lane];
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T q[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) mt.take(v[r][i]);
+      if (SPEC) {
+        Chunk<T, 8, false>::squares(v[r], q);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = FP<T>::add(acc[i], q[i]);
+      }
+    }
+  }
   for (; base + 256 <= n; base += 256) {
     T v[8], q[8];
 #pragma unroll

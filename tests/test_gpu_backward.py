@@ -119,3 +119,43 @@ def test_adjoint_central_differences(dev):
             fd[k] = np.dot(gv[a:b], oracle.normalize(xp, dim=n)[0] - oracle.normalize(xm, dim=n)[0]) / (2 * step)
         scale = np.linalg.norm(gv[a:b]) / r
         assert np.max(np.abs(fd - grad[a:b])) <= 1e-7 * scale, i
+
+
+@pytest.mark.parametrize("dim", [20, 300, 1500, 5000])
+def test_f64_backward_integer_pipe_limits(dev, dim):
+    """binary64 backward where the products y_k g_k and y_k dot leave or stay
+    in the range of the integer-pipe product: tiny and huge g components, tiny
+    y components (from inputs at the forward's limits), zero g, g with one
+    huge entry; dense rows and a ragged batch of the same vectors."""
+    from gpu_util import f64_range_edges
+    from paper_1606_06508_gb300 import api
+    rng = np.random.default_rng(dim)
+    count = max(40, min(600, 200000 // dim))
+    x = f64_range_edges(count, dim, seed=dim)
+    g = rng.standard_normal((count, dim))
+    for i in range(count):
+        kind = i % 6
+        if kind == 1:
+            g[i] *= 2.0 ** 600              # products near the top of the range with huge dot
+        elif kind == 2:
+            g[i] *= 2.0 ** -600             # tiny products
+        elif kind == 3:
+            g[i, int(rng.integers(dim))] = 2.0 ** -1060  # a subnormal g component
+        elif kind == 4:
+            g[i] = 0.0                      # dot = 0
+        elif kind == 5:
+            g[i, int(rng.integers(dim))] = 2.0 ** 1000
+    xt, gt = _to(dev, x), _to(dev, g)
+    y, h, c = api.normalize(xt, save=True)
+    grad = api.normalize_backward(y, gt, h, c)
+    oy, _, oh, oc = oracle.normalize(x.reshape(-1), dim=dim)
+    og = oracle.backward(oy, g.reshape(-1), oh, oc, dim=dim)
+    assert_bits(_np(grad), og, f"f64 d={dim} backward at the integer-pipe limits")
+    # the same vectors as a ragged batch (warp list)
+    off = np.arange(count + 1, dtype=np.int64) * dim
+    offt = _to(dev, off)
+    plan = api.Plan(count, xt.dtype)
+    plan.set_mapping(8, 8192, 256, 0)
+    yr, hr, cr = api.normalize(xt.reshape(-1), offt, save=True, plan=plan)
+    gr = api.normalize_backward(yr, gt.reshape(-1), hr, cr, offt, plan=plan)
+    assert_bits(_np(gr), og, f"f64 d={dim} ragged backward at the integer-pipe limits")
