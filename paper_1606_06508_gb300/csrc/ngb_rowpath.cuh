@@ -434,6 +434,9 @@ __device__ __forceinline__ void block_backward_stream(const T* __restrict__ yr, 
 }
 
 // ---------------------------------------------------------------------------
+// Rounds of 8 loads per lane that a binary32 streaming pass keeps in flight.
+constexpr int STREAM_ROUNDS = 2;
+
 // Streaming warp layout (any length).  Lane l reads the elements
 // k = 32 c + l, c = 0, 1, ..., eight chunks (256 elements) per round; slot
 // k mod 256 = 32 (c mod 8) + l is lane l's partial sum acc[c mod 8],
@@ -517,16 +520,17 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
 template <typename T, bool SCALED, bool EMU>
 __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
   int base = 0;
-  if (sizeof(T) == 4) {  // binary32: two rounds of loads in flight
-    for (; base + 512 <= n; base += 512) {
-      T v[2][8];
+  if (sizeof(T) == 4) {  // binary32: STREAM_ROUNDS rounds of loads in flight
+    constexpr int R = STREAM_ROUNDS;
+    for (; base + 256 * R <= n; base += 256 * R) {
+      T v[R][8];
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < R; ++r) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[r][i] = __ldcs(xr + base + 256 * r + 32 * i + lane);
       }
 #pragma unroll
-      for (int r = 0; r < 2; ++r) {
+      for (int r = 0; r < R; ++r) {
         if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v[r]);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -583,9 +587,9 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
     if (SPEC) Chunk<T, 8, false>::squares(v, acc);
   }
   int base = 256;
-  // binary32: two rounds (16 loads per lane) in flight per iteration, taken
-  // in ascending order, so the slot sums are unchanged
-  constexpr int R = sizeof(T) == 4 ? 2 : 1;
+  // binary32: STREAM_ROUNDS rounds (8 loads per lane each) in flight per
+  // iteration, taken in ascending order, so the slot sums are unchanged
+  constexpr int R = sizeof(T) == 4 ? STREAM_ROUNDS : 1;
   for (; base + 256 * R <= n; base += 256 * R) {
     T v[R][8];
 #pragma unroll
