@@ -68,6 +68,12 @@ def _load():
                 rot = getattr(lib, f"oracle_rotation_{sfx}")
                 rot.restype = ctypes.c_int
                 rot.argtypes = [P, ctypes.c_int64, P, P]
+                qt = getattr(lib, f"oracle_quotient3_{sfx}")
+                qt.restype = ctypes.c_int
+                qt.argtypes = [P, ctypes.c_int64, ctypes.c_int, P, P]
+                nv = getattr(lib, f"oracle_naive_{sfx}")
+                nv.restype = ctypes.c_int
+                nv.argtypes = [P, ctypes.c_int64, ctypes.c_int32, P]
             lib.oracle_ieee_check.restype = ctypes.c_int
             lib.oracle_ieee_check.argtypes = []
             _lib = lib
@@ -194,3 +200,29 @@ def rotation(q):
     if rc != 0:
         raise ValueError(f"oracle_rotation_{sfx} failed with code {rc}")
     return R, norm
+
+
+def quotient3(x, alg: int):
+    """The paper's quotient Algorithm 1 or 2 (Section 1) on vectors [count, 3]:
+    (y [count, 3], r [count])."""
+    x = np.ascontiguousarray(x)
+    sfx = _sfx(x.dtype)
+    count = x.size // 3
+    y = np.empty_like(x)
+    norm = np.empty(count, dtype=x.dtype)
+    rc = getattr(_load(), f"oracle_quotient3_{sfx}")(_ptr(x), count, int(alg), _ptr(y), _ptr(norm))
+    if rc != 0:
+        raise ValueError(f"oracle_quotient3_{sfx} failed with code {rc}")
+    return y, norm
+
+
+def naive(x, dim: int):
+    """The unscaled sequence of Table 4: y = x * (1 / sqrt(sum x_k^2)) on [count, dim]."""
+    x = np.ascontiguousarray(x)
+    sfx = _sfx(x.dtype)
+    count = x.size // dim
+    y = np.empty_like(x)
+    rc = getattr(_load(), f"oracle_naive_{sfx}")(_ptr(x), count, int(dim), _ptr(y))
+    if rc != 0:
+        raise ValueError(f"oracle_naive_{sfx} failed with code {rc}")
+    return y

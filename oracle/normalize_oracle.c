@@ -55,6 +55,7 @@
 #define SFX(name) name##_f32
 #define FABS fabsf
 #define SQRT sqrtf
+#define COPYSIGN copysignf
 #define TAU_MIN 0x1p-49f
 #define SIGMA_MIN 0x1p100f
 #define INV_SIGMA_MIN 0x1p-100f
@@ -69,6 +70,7 @@
 #undef SFX
 #undef FABS
 #undef SQRT
+#undef COPYSIGN
 #undef TAU_MIN
 #undef SIGMA_MIN
 #undef INV_SIGMA_MIN
@@ -84,6 +86,7 @@
 #define SFX(name) name##_f64
 #define FABS fabs
 #define SQRT sqrt
+#define COPYSIGN copysign
 #define TAU_MIN 0x1p-482
 #define SIGMA_MIN 0x1p592
 #define INV_SIGMA_MIN 0x1p-592

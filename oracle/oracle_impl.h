@@ -386,3 +386,92 @@ int SFX(oracle_rotation)(const REAL *q, int64_t count, REAL *R, REAL *norm)
     }
     return 0;
 }
+
+/* ---------------------------------------------------------------------- */
+/* The quotient algorithms the paper compares with (Section 1), for three
+ * components.  They are not the method; the library builds them to measure
+ * the paper's Table 3 ratio on the GPU.
+ *
+ * Algorithm 1 (robust quotient algorithm): m = max |x_k| (a NaN component
+ * never compares greater), the zero case returns r = 0 and x unchanged;
+ * otherwise t_k = x_k / m, r = m sqrt(t1 t1 + t2 t2 + t3 t3) and the
+ * outputs are x_k / r.  Reading: the last step divides the input components
+ * by r; the printed x_k <- x_k / r follows x_k <- x_k / m, which would return
+ * x_k / (m r), not a unit vector. */
+static void SFX(quotient1_3)(const REAL *x, REAL *y, REAL *r)
+{
+    REAL m = FABS(x[0]);
+    if (FABS(x[1]) > m) m = FABS(x[1]);
+    if (FABS(x[2]) > m) m = FABS(x[2]);
+    if (m == 0) { *r = 0; y[0] = x[0]; y[1] = x[1]; y[2] = x[2]; return; }
+    REAL t1 = x[0] / m, t2 = x[1] / m, t3 = x[2] / m;
+    REAL rr = m * SQRT(t1 * t1 + t2 * t2 + t3 * t3);
+    *r = rr;
+    y[0] = x[0] / rr;
+    y[1] = x[1] / rr;
+    y[2] = x[2] / rr;
+}
+
+/* Lines 3-7 of Algorithm 2 with pivot xp (the component of largest
+ * magnitude) and the other two components a, b in the roles of x1, x2. */
+static void SFX(quotient2_pivot)(REAL xp, REAL a, REAL b, REAL *r, REAL *yp, REAL *ya, REAL *yb)
+{
+    REAL q1 = a / xp, q2 = b / xp;
+    REAL h = SQRT(1 + q1 * q1 + q2 * q2);
+    *r = FABS(xp) * h;
+    REAL s = COPYSIGN((REAL)1, xp) / h;
+    *ya = q1 * s;
+    *yb = q2 * s;
+    *yp = s;
+}
+
+/* Algorithm 2 (fast robust quotient algorithm), branch by branch: pivot x3
+ * when |x1| > |x2| and |x3| > |x1|; pivot x1 (x1 and x3 exchange roles) when
+ * |x1| > |x2| otherwise; pivot x3 when |x3| >= |x2| >= |x1|; pivot x2 (x2 and
+ * x3 exchange roles) otherwise.  Reading: the zero return under "x3 = 0"
+ * also requires x1 = 0, as the text promises NaN outputs for NaN inputs and
+ * (NaN, 0, 0) reaches that test; with x1 = NaN the division gives NaN. */
+static void SFX(quotient2_3)(const REAL *x, REAL *y, REAL *r)
+{
+    REAL x1 = x[0], x2 = x[1], x3 = x[2];
+    if (FABS(x1) > FABS(x2)) {
+        if (FABS(x3) > FABS(x1)) SFX(quotient2_pivot)(x3, x1, x2, r, &y[2], &y[0], &y[1]);
+        else SFX(quotient2_pivot)(x1, x3, x2, r, &y[0], &y[2], &y[1]);
+    } else {
+        if (FABS(x3) >= FABS(x2)) {
+            if (x3 == 0 && x1 == 0) { *r = 0; y[0] = 0; y[1] = 0; y[2] = 0; return; }
+            SFX(quotient2_pivot)(x3, x1, x2, r, &y[2], &y[0], &y[1]);
+        } else {
+            SFX(quotient2_pivot)(x2, x1, x3, r, &y[1], &y[0], &y[2]);
+        }
+    }
+}
+
+/* Batch driver: x [count][3] -> y [count][3], r [count] (nullable);
+ * alg = 1 or 2.  Returns 0, or 1 for bad arguments. */
+int SFX(oracle_quotient3)(const REAL *x, int64_t count, int alg, REAL *y, REAL *norm)
+{
+    if (count < 0 || (alg != 1 && alg != 2)) return 1;
+    for (int64_t i = 0; i < count; ++i) {
+        REAL r;
+        if (alg == 1) SFX(quotient1_3)(x + 3 * i, y + 3 * i, &r);
+        else SFX(quotient2_3)(x + 3 * i, y + 3 * i, &r);
+        if (norm) norm[i] = r;
+    }
+    return 0;
+}
+
+/* The naive sequence of the paper's Table 4 (no scaling): s = x1 x1 + ... +
+ * xn xn (left to right), h = 1 / sqrt(s), y_k = h x_k; x [count][dim]. */
+int SFX(oracle_naive)(const REAL *x, int64_t count, int32_t dim, REAL *y)
+{
+    if (count < 0 || dim < 1) return 1;
+    for (int64_t i = 0; i < count; ++i) {
+        const REAL *v = x + (int64_t)dim * i;
+        REAL sum = v[0] * v[0];
+        for (int32_t k = 1; k < dim; ++k) sum = sum + v[k] * v[k];
+        REAL h = 1 / SQRT(sum);
+        for (int32_t k = 0; k < dim; ++k) y[(int64_t)dim * i + k] = h * v[k];
+    }
+    return 0;
+}

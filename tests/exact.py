@@ -108,8 +108,10 @@ class Result:
         return self.ok_direction and self.ok_norm and self.ok_finite and self.ok_sin and self.ok_pairs
 
 
-def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False) -> Result:
-    """Check one finite, nonzero input vector x and its computed (x^, r^)."""
+def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False, dir_bound_u=None, norm_bound_u=None) -> Result:
+    """Check one finite, nonzero input vector x and its computed (x^, r^).
+    dir_bound_u / norm_bound_u replace the paper's bounds (Lemmas 1, 2, 4),
+    for other algorithms checked with the same machinery."""
     n = len(x)
     xs = [fr(v) for v in x]
     if not all(math.isfinite(float(v)) for v in yhat):
@@ -121,7 +123,7 @@ def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False) -> Result:
     A = sum(v * v for v in ys)
     P = sum(a * b for a, b in zip(ys, xs))
     # ||x^ - x/r||^2 = A - 2P/r + 1 <= (B u)^2  <=>  L <= 2P/r  <=>  L sqrt(s) <= 2P
-    B = direction_bound(n, u)
+    B = direction_bound(n, u) if dir_bound_u is None else Fr(dir_bound_u)
     L = A + 1 - (B * u) ** 2
     ok_dir = _le_sqrt_lhs(L, 2 * P, s)
     r_approx = _sqrt_approx(s)
@@ -136,7 +138,7 @@ def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False) -> Result:
     # norm: finite and within (1 + n/2) r u (+ alpha/2 when 2r <= 3nu/2), claimed
     # when (1 + (1 + n/2) u) r <= omega
     rh = float(rhat)
-    K = norm_bound(n, u) * u
+    K = (norm_bound(n, u) if norm_bound_u is None else Fr(norm_bound_u)) * u
     finite_claim = (1 + K) ** 2 * s <= fmt.omega ** 2
     ok_fin = rh != 0.0 and (math.isfinite(rh) or not finite_claim)
     ok_norm = True

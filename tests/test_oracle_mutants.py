@@ -1,8 +1,9 @@
 """The pins must catch plausible mistakes in the oracle.  Each case plants one
 mistake in a copy of the oracle's C source (a dropped term, a wrong
 comparison, a swapped constant, a wrong sign, a transposed operand, a skipped
-rounding step, the literal reading of Algorithm 7), builds it, and runs the
-pin suite against it in a subprocess: the suite has to fail.  CPU only."""
+rounding step, the literal reading of Algorithm 7, misplaced outputs of the
+quotient algorithms), builds it, and runs the pin suites against it in a
+subprocess: they have to fail.  CPU only."""
 import os
 import shutil
 import subprocess
@@ -42,6 +43,14 @@ MUTANTS = [
      "REAL tk = g[k] - y[k] * dot;", "REAL tk = g[k] + y[k] * dot;"),
     ("rotation matrix with a transposed operand", "oracle_impl.h",
      "R[1] = 2 * (q1 * q2 - q3 * q4);", "R[1] = 2 * (q1 * q3 - q2 * q4);"),
+    ("Algorithm 2 with pivot x1 writes its outputs to the wrong places", "oracle_impl.h",
+     "else SFX(quotient2_pivot)(x1, x3, x2, r, &y[0], &y[2], &y[1]);",
+     "else SFX(quotient2_pivot)(x1, x3, x2, r, &y[2], &y[0], &y[1]);"),
+    ("Algorithm 2 drops the sign of the pivot", "oracle_impl.h",
+     "REAL s = COPYSIGN((REAL)1, xp) / h;", "REAL s = 1 / h;"),
+    ("Algorithm 1 divides the scaled components by r", "oracle_impl.h",
+     "    y[0] = x[0] / rr;\n    y[1] = x[1] / rr;\n    y[2] = x[2] / rr;",
+     "    y[0] = t1 / rr;\n    y[1] = t2 / rr;\n    y[2] = t3 / rr;"),
 ]
 
 
@@ -66,6 +75,7 @@ def test_pins_catch_planted_mistake(cc, tmp_path, name, fname, old, new):
     lib = str(tmp_path / "liboracle_mutant.so")
     subprocess.run([compiler, *cflags, str(tmp_path / "normalize_oracle.c"), "-o", lib, "-lm"], check=True)
     env = dict(os.environ, NGB_ORACLE_LIB=lib)
-    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle_pins.py"), "-x", "-q",
-                          "-p", "no:cacheprovider"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    out = subprocess.run([sys.executable, "-m", "pytest", os.path.join(HERE, "test_oracle_pins.py"),
+                          os.path.join(HERE, "test_oracle_quotient_pins.py"), "-x", "-q", "-p", "no:cacheprovider"],
+                         cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode != 0, f"the pins did not catch: {name}\n{out.stdout[-2000:]}"
