@@ -421,6 +421,46 @@ WORKLOAD_NAMES = ["quat", "fwdbwd_quat", "rows_f32", "rows_f64", "ragged_f32", "
                   "vec3_f64"]
 
 
+def paper_tables(torch, L, synth, s):
+    """GPU analogues of the paper's Tables 3 and 4 (Appendix A): on 2^24
+    three-component vectors with N(0,1) components, the time of the quotient
+    Algorithms 1 and 2 over the time of the scaling algorithm (Table 3), and
+    the time of the scaling algorithm over the naive sequence (Table 4);
+    CUDA events, median of 10 launches each."""
+    out = {}
+    n = 1 << 24
+    for name, dt in (("f32", torch.float32), ("f64", torch.float64)):
+        x = synth.normal_like_torch((n, 3), dt, seed=77, device="cuda")
+        y = torch.empty_like(x)
+        r = torch.empty(n, dtype=dt, device="cuda")
+        xp, yp, rp = x.data_ptr(), y.data_ptr(), r.data_ptr()
+        norm = L.normalize_f32 if name == "f32" else L.normalize_f64
+        quot = L.quotient_normalize3_f32 if name == "f32" else L.quotient_normalize3_f64
+        naive = L.naive_normalize_f32 if name == "f32" else L.naive_normalize_f64
+        fns = {
+            "scaling": lambda: L.check(norm(xp, yp, rp, None, None, n, 3, None, None, 0, s.cuda_stream), "scaling"),
+            "scaling_no_norm": lambda: L.check(norm(xp, yp, None, None, None, n, 3, None, None, 0, s.cuda_stream),
+                                               "scaling"),
+            "quotient_alg1": lambda: L.check(quot(xp, yp, rp, n, 1, s.cuda_stream), "alg1"),
+            "quotient_alg2": lambda: L.check(quot(xp, yp, rp, n, 2, s.cuda_stream), "alg2"),
+            "naive": lambda: L.check(naive(xp, yp, n, 3, s.cuda_stream), "naive"),
+        }
+        ms = {}
+        for k, fn in fns.items():
+            fn()
+            torch.cuda.synchronize()
+            ms[k] = statistics.median(time_events(fn, 10, s))
+        out[f"paper_tables_vec3_{name}"] = {
+            "vectors": n, "ms": ms,
+            "table3_time_quotient_over_scaling": {"alg1": ms["quotient_alg1"] / ms["scaling"],
+                                                  "alg2": ms["quotient_alg2"] / ms["scaling"]},
+            "table4_time_scaling_over_naive": ms["scaling_no_norm"] / ms["naive"],
+            "note": "Table 3: scaling and quotient algorithms return y and r; Table 4: both return y only"}
+        del x, y, r
+        torch.cuda.empty_cache()
+    return out
+
+
 def extras(torch, L, api, synth, peak, rate):
     """Secondary measurements on this GPU (each step repeated 10 times,
     CUDA events): the other workloads, the copy ceiling, the naive algorithm."""
@@ -446,6 +486,7 @@ def extras(torch, L, api, synth, peak, rate):
         except Exception as e:  # report, do not hide
             out[name] = {"error": repr(e)}
         torch.cuda.empty_cache()
+    out.update(paper_tables(torch, L, synth, s))
     a = torch.empty(QUAT_COUNT * 4, device="cuda")
     b = torch.empty_like(a)
     a.normal_()

@@ -175,6 +175,24 @@ ngb_status ngb_copy(void* dst, const void* src, int64_t bytes, ngb_stream_t stre
 ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream);
 ngb_status naive_normalize_f64(const double* x, double* y, int64_t count, int32_t dim, ngb_stream_t stream);
 
+/* The quotient algorithms the paper compares its method with (Section 1,
+ * Algorithms 1 and 2), for three components; not the method, built to
+ * measure the paper's Table 3 ratio time(quotient) / time(scaling).
+ * alg = 1: m = max |x_k| (zero: r = 0, y = x); t_k = x_k / m; r = m sqrt(t1^2 +
+ *          t2^2 + t3^2); y_k = x_k / r (the input components divided by r).
+ * alg = 2: pivot p = the component of largest magnitude, in the printed
+ *          branch order; q = (other components) / x_p; h = sqrt(1 + q1^2 + q2^2);
+ *          r = |x_p| h; y_p = sign(x_p) / h, other y = q s; the zero return
+ *          when x1 = x3 = 0 (so a NaN input gives NaN outputs).
+ * x, y: [count][3] device arrays owned by the caller (y may alias x); norm:
+ * [count] device array or NULL.  Every step is one correctly rounded IEEE
+ * operation.  Errors: NGB_ERR_INVALID_ARG for count < 0, alg not 1 or 2, or a
+ * null x or y; NGB_ERR_CUDA for a launch failure. */
+ngb_status quotient_normalize3_f32(const float* x, float* y, float* norm, int64_t count, int32_t alg,
+                                   ngb_stream_t stream);
+ngb_status quotient_normalize3_f64(const double* x, double* y, double* norm, int64_t count, int32_t alg,
+                                   ngb_stream_t stream);
+
 /* Measurement aid (not the method): the binary64 pipe's throughput.  Launches
  * `blocks` blocks of 256 threads; each thread runs 4 independent chains of
  * `iters` steps a <- RN(RN(a * b) + c), two FP64 instructions per step, and

@@ -53,6 +53,8 @@ PROTOTYPES = {
     "normalize_to_rotation_f64": (ST, [P, P, P, I64, P]),
     "ngb_copy": (ST, [P, P, I64, P]),
     "ngb_fp64_probe": (ST, [P, I32, I32, P, P]),
+    "quotient_normalize3_f32": (ST, [P, P, P, I64, I32, P]),
+    "quotient_normalize3_f64": (ST, [P, P, P, I64, I32, P]),
     "naive_normalize_f32": (ST, [P, P, I64, I32, P]),
     "naive_normalize_f64": (ST, [P, P, I64, I32, P]),
     "normalize_ragged_f32_noalloc": (ST, [P, P, P, P, P, I64, P, U32, P]),
@@ -122,6 +124,8 @@ normalize_to_rotation_f32 = _fwd("normalize_to_rotation_f32")
 normalize_to_rotation_f64 = _fwd("normalize_to_rotation_f64")
 ngb_copy = _fwd("ngb_copy")
 ngb_fp64_probe = _fwd("ngb_fp64_probe")
+quotient_normalize3_f32 = _fwd("quotient_normalize3_f32")
+quotient_normalize3_f64 = _fwd("quotient_normalize3_f64")
 naive_normalize_f32 = _fwd("naive_normalize_f32")
 naive_normalize_f64 = _fwd("naive_normalize_f64")
 normalize_ragged_f32_noalloc = _fwd("normalize_ragged_f32_noalloc")

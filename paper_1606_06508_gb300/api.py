@@ -228,3 +228,17 @@ def naive_normalize(x: torch.Tensor, out: torch.Tensor | None = None):
     fn = L.naive_normalize_f32 if sfx == "f32" else L.naive_normalize_f64
     L.check(fn(x.data_ptr(), y.data_ptr(), x.numel() // dim, dim, _stream()), f"naive_normalize_{sfx}")
     return y
+
+
+def quotient_normalize3(x: torch.Tensor, alg: int, out: torch.Tensor | None = None, return_norm: bool = False):
+    """The paper's quotient Algorithm 1 or 2 (Section 1) on vectors [..., 3]."""
+    _check_tensor(x, "x")
+    sfx, _ = _sfx(x.dtype)
+    if x.shape[-1] != 3:
+        raise ValueError("the quotient algorithms take three components")
+    count = x.numel() // 3
+    y = torch.empty_like(x) if out is None else out
+    norm = torch.empty(count, dtype=x.dtype, device=x.device) if return_norm else None
+    fn = L.quotient_normalize3_f32 if sfx == "f32" else L.quotient_normalize3_f64
+    L.check(fn(x.data_ptr(), y.data_ptr(), _ptr(norm), count, alg, _stream()), f"quotient_normalize3_{sfx}")
+    return (y, norm) if return_norm else y

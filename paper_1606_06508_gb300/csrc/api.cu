@@ -184,6 +184,17 @@ ngb_status backward(const T* y, const T* g, const T* h, const int8_t* code, T* g
 }  // namespace
 
 // ---------------------------------------------------------------------------
+template <typename T>
+static ngb_status quotient3_impl(const T* x, T* y, T* norm, int64_t count, int32_t alg, ngb_stream_t stream,
+                                 const char* name) {
+  g_last_error.clear();
+  if (count < 0 || (alg != 1 && alg != 2)) return fail(NGB_ERR_INVALID_ARG, "count < 0 or alg not 1 or 2");
+  if (count == 0) return NGB_OK;
+  if (!x || !y) return fail(NGB_ERR_INVALID_ARG, "x and y are required");
+  cudaError_t e = ngb::launch_quotient3<T>(x, y, norm, count, alg, cs(stream));
+  return e == cudaSuccess ? NGB_OK : cuda_fail(e, name);
+}
+
 extern "C" {
 
 ngb_status normalize_f32(const float* x, float* y, float* norm, float* saved_h, int8_t* saved_code, int64_t count,
@@ -441,6 +452,16 @@ ngb_status ngb_fp64_probe(double* out, int32_t blocks, int32_t iters, int64_t* f
   if (fp64_ops) *fp64_ops = (int64_t)blocks * 256 * 4 * 2 * (int64_t)iters;
   cudaError_t e = ngb::launch_fp64_probe(out, blocks, iters, cs(stream));
   return e == cudaSuccess ? NGB_OK : cuda_fail(e, "fp64 probe launch");
+}
+
+ngb_status quotient_normalize3_f32(const float* x, float* y, float* norm, int64_t count, int32_t alg,
+                                   ngb_stream_t stream) {
+  return quotient3_impl<float>(x, y, norm, count, alg, stream, "quotient_normalize3_f32 launch");
+}
+
+ngb_status quotient_normalize3_f64(const double* x, double* y, double* norm, int64_t count, int32_t alg,
+                                   ngb_stream_t stream) {
+  return quotient3_impl<double>(x, y, norm, count, alg, stream, "quotient_normalize3_f64 launch");
 }
 
 ngb_status naive_normalize_f32(const float* x, float* y, int64_t count, int32_t dim, ngb_stream_t stream) {

@@ -4,6 +4,7 @@
 
 #include "ngb_internal.h"
 #include "ngb_rowpath.cuh"
+#include "ngb_quotient.cuh"
 
 namespace ngb {
 
@@ -202,5 +203,53 @@ cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s
   k_fp64_probe<<<blocks, FP64_PROBE_THREADS, 0, s>>>(out, iters);
   return cudaGetLastError();
 }
+
+// Quotient algorithms on [count][3]: a tile of 256 vectors staged through
+// shared memory (coalesced loads and stores of the AoS triples), one vector
+// per thread.
+template <typename T, int ALG>
+__global__ void __launch_bounds__(256) k_quotient3(const T* __restrict__ x, T* y, T* norm, int64_t count) {
+  constexpr int NT = 256;
+  __shared__ T tile[NT * 3];
+  const int t = threadIdx.x;
+  for (int64_t v0 = (int64_t)blockIdx.x * NT; v0 < count; v0 += (int64_t)gridDim.x * NT) {
+    const int nv = (int)((count - v0) < NT ? (count - v0) : NT);
+    const T* src = x + v0 * 3;
+    for (int i = t; i < nv * 3; i += NT) tile[i] = __ldcs(src + i);
+    __syncthreads();
+    T yv[3], r = T(0);
+    if (t < nv) {
+      const T xv[3] = {tile[3 * t], tile[3 * t + 1], tile[3 * t + 2]};
+      if (ALG == 1) quotient1_3<T>(xv, yv, r);
+      else quotient2_3<T>(xv, yv, r);
+      if (norm) norm[v0 + t] = r;
+    }
+    __syncthreads();
+    if (t < nv) {
+      tile[3 * t] = yv[0];
+      tile[3 * t + 1] = yv[1];
+      tile[3 * t + 2] = yv[2];
+    }
+    __syncthreads();
+    T* dst = y + v0 * 3;
+    for (int i = t; i < nv * 3; i += NT) __stcs(dst + i, tile[i]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+cudaError_t launch_quotient3(const T* x, T* y, T* norm, int64_t count, int alg, cudaStream_t s) {
+  int per_sm = 0;
+  if (alg == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quotient3<T, 1>, 256, 0);
+  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quotient3<T, 2>, 256, 0);
+  const int64_t need = (count + 255) / 256;
+  const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
+  const int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  if (alg == 1) k_quotient3<T, 1><<<grid, 256, 0, s>>>(x, y, norm, count);
+  else k_quotient3<T, 2><<<grid, 256, 0, s>>>(x, y, norm, count);
+  return cudaGetLastError();
+}
+template cudaError_t launch_quotient3<float>(const float*, float*, float*, int64_t, int, cudaStream_t);
+template cudaError_t launch_quotient3<double>(const double*, double*, double*, int64_t, int, cudaStream_t);
 
 }  // namespace ngb

@@ -33,6 +33,7 @@ template <> struct FP<float> {
   __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
   __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
   __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+  __device__ __forceinline__ static float div(float a, float b) { return __fdiv_rn(a, b); }
   __device__ __forceinline__ static float sqrt(float a) { return __fsqrt_rn(a); }
   __device__ __forceinline__ static float rcp(float a) { return __frcp_rn(a); }
   __device__ __forceinline__ static float abs(float a) { return fabsf(a); }
@@ -48,6 +49,7 @@ template <> struct FP<double> {
   __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
   __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
   __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+  __device__ __forceinline__ static double div(double a, double b) { return __ddiv_rn(a, b); }
   __device__ __forceinline__ static double sqrt(double a) { return __dsqrt_rn(a); }
   __device__ __forceinline__ static double rcp(double a) { return __drcp_rn(a); }
   __device__ __forceinline__ static double abs(double a) { return fabs(a); }

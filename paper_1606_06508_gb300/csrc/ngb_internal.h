@@ -54,6 +54,8 @@ int ragged_full_wave(const RaggedMapping& map, bool backward);
 cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s);
 cudaError_t launch_fp64_probe(double* out, int blocks, int iters, cudaStream_t s);
 template <typename T>
+cudaError_t launch_quotient3(const T* x, T* y, T* norm, int64_t count, int alg, cudaStream_t s);
+template <typename T>
 cudaError_t launch_naive(const T* x, T* y, int64_t count, int dim, cudaStream_t s);
 template <typename T>
 cudaError_t launch_rotation(const T* q, T* R, T* norm, int64_t count, cudaStream_t s);
