@@ -411,7 +411,7 @@ def build_work(name, count, rank, torch, L, api, synth):
             L.check(L.normalize_f64(x.data_ptr(), y.data_ptr(), None, None, None, cnt, 3, None, None, 0,
                                     s.cuda_stream), "vec3")
         return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
-                    units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_staged<double,3>", launches=1,
+                    units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_direct<double,3>", launches=1,
                     step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 3, k=cnt), flush=True,
                     bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
     raise ValueError(f"unknown workload {name}")

@@ -47,52 +47,40 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_vec16(const T* __restri
   }
 }
 
-// dim <= 4, a tile of SMALL_THREADS vectors staged through shared memory
-// (16-byte loads and stores when x and y are 16-byte aligned).
+// dim <= 4, one vector per thread read and written as D scalars (a warp's
+// loads cover consecutive 128-byte lines; L1 serves the repeated lines), U
+// vectors in flight per thread: for D = 1, 2, 3 and unaligned quaternions.
 template <typename T, int D>
-__global__ void __launch_bounds__(SMALL_THREADS) k_small_staged(const T* __restrict__ x, T* y, VecOut<T> out,
-                                                                 int64_t count, int quat_zero, int vec16) {
-  constexpr int NT = SMALL_THREADS;
-  constexpr int W = 16 / sizeof(T);
-  constexpr int NC = NT * D / W;
-  __shared__ __align__(16) T tile[NT * D];
-  const int t = threadIdx.x;
-  for (int64_t v0 = (int64_t)blockIdx.x * NT; v0 < count; v0 += (int64_t)gridDim.x * NT) {
-    const int nv = (int)((count - v0) < NT ? (count - v0) : NT);
-    const T* src = x + v0 * D;
-    if (vec16 && nv == NT) {
-      for (int i = t; i < NC; i += NT)
-        reinterpret_cast<uint4*>(tile)[i] = __ldcs(reinterpret_cast<const uint4*>(src) + i);
-    } else {
-      for (int i = t; i < nv * D; i += NT) tile[i] = src[i];
-    }
-    __syncthreads();
-    T yv[D];
-    if (t < nv) {
-      T xv[D], r, h;
+__global__ void __launch_bounds__(SMALL_THREADS) k_small_direct(const T* __restrict__ x, T* y, VecOut<T> out,
+                                                                 int64_t count, int quat_zero) {
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+    T xv[U][D];
 #pragma unroll
-      for (int k = 0; k < D; ++k) xv[k] = tile[t * D + k];
-      const int code = normalize_small<T, D>(xv, yv, r, h, quat_zero != 0);
-      out.put(v0 + t, r, h, code);
-    }
-    __syncthreads();
-    if (y) {
-      if (t < nv) {
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
 #pragma unroll
-        for (int k = 0; k < D; ++k) tile[t * D + k] = yv[k];
+        for (int k = 0; k < D; ++k) xv[u][k] = __ldcs(x + i * D + k);
       }
-      __syncthreads();
-      T* dst = y + v0 * D;
-      if (vec16 && nv == NT) {
-        for (int i = t; i < NC; i += NT)
-          __stcs(reinterpret_cast<uint4*>(dst) + i, reinterpret_cast<const uint4*>(tile)[i]);
-      } else {
-        for (int i = t; i < nv * D; i += NT) dst[i] = tile[i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      if (i < count) {
+        T yv[D], r, h;
+        const int code = normalize_small<T, D>(xv[u], yv, r, h, quat_zero != 0);
+        if (y) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) __stcs(y + i * D + k, yv[k]);
+        }
+        out.put(i, r, h, code);
       }
-      __syncthreads();
     }
   }
 }
+
 
 template <typename T, int D>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_bwd(const T* __restrict__ y, const T* __restrict__ g,
@@ -254,9 +242,9 @@ cudaError_t launch_small_fwd(const T* x, T* y, VecOut<T> out, int64_t count, boo
     }
   }
   {
-    auto k = k_small_staged<T, D>;
-    const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS);
-    k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero, vec16 ? 1 : 0);
+    auto k = k_small_direct<T, D>;
+    const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS);  // small batches: one vector per thread
+    k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero);
   }
   return cudaGetLastError();
 }
