@@ -24,6 +24,10 @@ constexpr int SMALL_THREADS = 256;
 // the backward (two 16-byte loads per quaternion) is best at 4 (6: 0.83).
 constexpr int VEC16_IN_FLIGHT = 6;
 constexpr int BWD16_IN_FLIGHT = 4;
+// rows per warp with their loads in flight together in k_rows_warp (measured
+// on 2^20 binary32 rows of 256: 1 row 0.887 of the copy bandwidth, 2: 0.861,
+// 3: 0.874, 4: 0.855)
+constexpr int ROWS_IN_FLIGHT = 1;
 
 // ---------------------------------------------------------------------------
 // dim <= 4, one 16-byte vector per thread, U vectors in flight per thread.
@@ -161,8 +165,22 @@ __global__ void __launch_bounds__(256) k_rows_warp(const T* __restrict__ x, T* y
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t row = w0; row < count; row += nw)
-    warp_forward<T, V, CH>(x + row * n, y ? y + row * n : nullptr, n, lane, out, row);
+  // ROWS_IN_FLIGHT rows per warp: their loads are all issued before the first
+  // row is reduced
+  constexpr int R = ROWS_IN_FLIGHT;
+  for (int64_t row0 = w0; row0 < count; row0 += nw * R) {
+    T v[R][CH][V];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = row0 + r * nw;
+      if (row < count) warp_load<T, V, CH>(x + row * n, n, lane, v[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int64_t row = row0 + r * nw;
+      if (row < count) warp_forward_loaded<T, V, CH>(v[r], x + row * n, y ? y + row * n : nullptr, n, lane, out, row);
+    }
+  }
 }
 
 template <typename T, int V, int CH>

@@ -823,14 +823,11 @@ __device__ __forceinline__ void warp_forward_tail(T (&v)[CH][V], T* yr, int n, i
   if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }
 
-
-// Forward, one warp per vector of length 5 <= n <= 32 V CH.  yr may be null
-// (norm only).  The whole warp must call it with the same arguments.
+// Forward, one warp per vector of length 5 <= n <= 32 V CH (warp_forward).
+// yr may be null (norm only).  The whole warp must call it with the same
+// arguments.  warp_load reads the vector into registers, zero-padded.
 template <typename T, int V, int CH>
-__device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
-                                             const VecOut<T>& out, int64_t vec) {
-  T v[CH][V];
-  MagTrack<T> mt;
+__device__ __forceinline__ void warp_load(const T* __restrict__ xr, int n, int lane, T (&v)[CH][V]) {
 #pragma unroll
   for (int c = 0; c < CH; ++c) {
     const int k0 = 32 * V * c + V * lane;
@@ -840,6 +837,17 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
 #pragma unroll
       for (int e = 0; e < V; ++e) v[c][e] = T(0);
     }
+  }
+}
+
+// The same, on a row already in registers (warp_load), so that a kernel can
+// have several rows' loads in flight before it computes.
+template <typename T, int V, int CH>
+__device__ __forceinline__ void warp_forward_loaded(T (&v)[CH][V], const T* __restrict__ xr, T* yr, int n, int lane,
+                                                    const VecOut<T>& out, int64_t vec) {
+  MagTrack<T> mt;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
 #pragma unroll
     for (int e = 0; e < V; ++e) mt.take(v[c][e]);  // zero padding changes neither m nor the zero test
   }
@@ -877,6 +885,14 @@ __device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, in
     return;
   }
   warp_forward_tail<T, V, CH, sizeof(T) == 8>(v, yr, n, lane, out, vec, code);
+}
+
+template <typename T, int V, int CH>
+__device__ __forceinline__ void warp_forward(const T* __restrict__ xr, T* yr, int n, int lane,
+                                             const VecOut<T>& out, int64_t vec) {
+  T v[CH][V];
+  warp_load<T, V, CH>(xr, n, lane, v);
+  warp_forward_loaded<T, V, CH>(v, xr, yr, n, lane, out, vec);
 }
 
 // Backward pass 1 (dot = CR(y_k g_k)), streaming.  EMU (binary64): the
