@@ -70,15 +70,22 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
       if (lane == 0) wcount[w][k] = __popc(ball[k]);
     }
     __syncthreads();
-    if (t < 3) {
-      int sum = 0;
-      for (int ww = 0; ww < CLASSIFY_THREADS / 32; ++ww) {
-        const int c = wcount[ww][t];
-        wbase[ww][t] = sum;
-        sum += c;
+    if (w == 0) {  // per bucket: exclusive scan of the 32 warp counts by shuffles, one atomic per block
+      static_assert(CLASSIFY_THREADS == 1024, "one warp count per lane");
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int c = wcount[lane][k];
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        int g = 0;
+        if (lane == 31 && incl) g = atomicAdd(&sc.counts[k], incl);
+        g = __shfl_sync(FULL, g, 31);
+        wbase[lane][k] = g + incl - c;
       }
-      const int g = sum ? atomicAdd(&sc.counts[t], sum) : 0;
-      for (int ww = 0; ww < CLASSIFY_THREADS / 32; ++ww) wbase[ww][t] += g;
     }
     __syncthreads();
     if (b >= 0) {
