@@ -286,7 +286,7 @@ def fp64_rate(torch, L):
     s = torch.cuda.current_stream()
 
     def fn():
-        L.check(L.ngb_fp64_probe(out.data_ptr(), blocks, 4096, ctypes.byref(ops), s.cuda_stream), "fp64 probe")
+        L.check(L.ngb_fp64_probe(out.data_ptr(), blocks, 1024, ctypes.byref(ops), s.cuda_stream), "fp64 probe")
     fn()
     torch.cuda.synchronize()
     t = statistics.median(time_events(fn, 5, s)) * 1e-3
@@ -622,8 +622,10 @@ def run_ours(args):
             "gpu_launches": args.steps * w.launches,
             "clocks": clocks,
         }
-        rate = fp64_rate(torch, L)
-        result["fp64_ops_per_s"] = rate
+        need_rate = w.dp_ops is not None or (world == 1 and not args.no_extras and args.workload == "quat")
+        rate = fp64_rate(torch, L) if need_rate else None
+        if rate:
+            result["fp64_ops_per_s"] = rate
         dp = dp_roofline(w, ms / args.steps, rate)
         if dp:
             result["dp_roofline"] = dp
