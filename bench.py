@@ -303,7 +303,7 @@ def dp_roofline(w, ms_per_step, rate):
             "peak_source": "measured live: ngb_fp64_probe (dmul + dadd chains)"}
 
 
-def build_work(name, count, rank, torch, L, api, synth):
+def build_work(name, count, rank, torch, L, api, synth, mapping=None):
     dev = torch.device("cuda", torch.cuda.current_device())
     s = torch.cuda.current_stream()
     seed = 1000 * rank
@@ -369,7 +369,11 @@ def build_work(name, count, rank, torch, L, api, synth):
         x = synth.ragged_values_torch(lengths, dt, seed=3 + seed)
         y = torch.empty_like(x)
         plan = api.Plan(cnt, dt)
-        mapping = plan.autotune(off)
+        if mapping:  # a fixed mapping (profiling): no autotuning launches before the timed ones
+            plan.set_mapping(*mapping)
+            mapping = plan.mapping
+        else:
+            mapping = plan.autotune(off)
         fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
         s_bytes = x.element_size()
         if not fb:
@@ -553,7 +557,7 @@ def run_ours(args):
 
     peak, peak_src = peaks()
     s = torch.cuda.current_stream()
-    w = build_work(args.workload, args.count, rank, torch, L, api, synth)
+    w = build_work(args.workload, args.count, rank, torch, L, api, synth, mapping=args.mapping)
     flush = None
     if w.flush:
         flush_buf = torch.empty(2 * L2_BYTES // 4, device=dev)
@@ -685,6 +689,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=WORKLOAD_NAMES, default="quat")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--mapping", type=lambda v: [int(t) for t in v.split(",")], default=None,
+                    help="ragged workloads: thread_max,warp_max,block_threads,grid_blocks instead of autotuning "
+                         "(profiling)")
     ap.add_argument("--count", type=int, default=QUAT_COUNT,
                     help="units per GPU; the default selects each workload's full size (2^26 quaternions for the "
                          "headline); smaller values only for profiling")
