@@ -421,6 +421,22 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
     raise ValueError(f"unknown workload {name}")
 
 
+def full_size_desc(name):
+    """The workload description of the full-size line, shared by both arms."""
+    return {
+        "quat": "2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 wide-exponent/N(0,1) components",
+        "fwdbwd_quat": f"{1 << 24} binary32 quaternions, forward (saving h and code) + backward",
+        "rows_f32": f"{1 << 20} rows of 256 f32, forward, N(0,1) x 2^s per row",
+        "rows_f64": f"{1 << 19} rows of 256 f64, forward, N(0,1) x 2^s per row",
+        "ragged_f32": "4000000 ragged f32 vectors (40% of length 2-4, else log-uniform [5,4096]), int64 offsets, "
+                      "forward, one persistent launch after the classifier",
+        "ragged_f64": "4000000 ragged f64 vectors (40% of length 2-4, else log-uniform [5,4096]), int64 offsets, "
+                      "forward, one persistent launch after the classifier",
+        "fwdbwd_ragged_f64": "500000 ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
+        "vec3_f64": "65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
+    }[name]
+
+
 WORKLOAD_NAMES = ["quat", "fwdbwd_quat", "rows_f32", "rows_f64", "ragged_f32", "ragged_f64", "fwdbwd_ragged_f64",
                   "vec3_f64"]
 
@@ -528,7 +544,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.workload.endswith("f64") else "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "reference_step": f"{units} vectors of the same recipe (bounded sample)"},
+        "config": {"workload": full_size_desc(args.workload), "workload_name": args.workload,
+                   "reference_step": f"{units} vectors of the same recipe (bounded sample)"},
         "cpu_baseline": {"value": v, "unit": "vectors/s", "cores": threads, "kind": "oracle",
                          "sample": f"{units} vectors per step, oracle on {threads} host threads over contiguous ranges"},
         "e2e": {"value": v, "unit": "vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -609,7 +626,9 @@ def run_ours(args):
             "metric": METRIC, "value": world * args.steps * w.units / secs, "unit": "vectors/s", "n_gpus": world,
             "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
-            "config": {"workload": w.desc, "vectors_per_gpu": w.units, "algorithmic_bytes_per_step_per_gpu": w.bytes,
+            "config": {"workload": full_size_desc(args.workload) if args.count == QUAT_COUNT else w.desc,
+                       "workload_name": args.workload,
+                       "vectors_per_gpu": w.units, "algorithmic_bytes_per_step_per_gpu": w.bytes,
                        "bytes_model": w.bytes_model,
                        "l2": ("L2 flushed between steps (256 MB write), outside the timed intervals" if w.flush else
                               "inputs larger than L2 (126 MB); no flush"),
