@@ -174,6 +174,26 @@ struct RaggedArgs {
 // Forward persistent kernel, B threads per block (128 or 256).  Resident
 // threads per SM requested: 5 x 256 for binary32 (at most 48 registers),
 // 3 x 256 for binary64 (at most 80, no spills).
+// L2 prefetch of the next warp item's vector (within the ticket) while the
+// current item runs.  Measured on the ragged workloads: binary32 0.798 ->
+// 0.846 of the copy bandwidth (a whole ticket at once: 0.829; the next
+// ticket taken one ahead to prefetch across tickets: 0.827); binary64, bound
+// by the FP64 pipe, 0.401 -> 0.388: off.
+constexpr bool WARP_PREFETCH_F32 = true, WARP_PREFETCH_F64 = false;
+template <typename T>
+__host__ __device__ constexpr bool warp_prefetch() { return sizeof(T) == 4 ? WARP_PREFETCH_F32 : WARP_PREFETCH_F64; }
+
+// Prefetch vector `vec` of the batch into L2, one 128-byte line per lane and
+// step (every address lies inside the vector).
+template <typename T>
+__device__ __forceinline__ void prefetch_item_l2(const RaggedArgs<T>& a, int64_t vec, int lane) {
+  const int64_t s = a.off[vec], e = a.off[vec + 1];
+  const char* p = reinterpret_cast<const char*>(a.x + s);
+  const int64_t bytes = (e - s) * (int64_t)sizeof(T);
+  for (int64_t b = (int64_t)lane * 128; b < bytes; b += 32 * 128)
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p + b));
+}
+
 template <typename T>
 constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 3 * 256 / B; }
 
@@ -199,7 +219,8 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
     block_forward_stream<T, B>(a.x + s, a.y ? a.y + s : nullptr, n, a.out, vec, sh);
   }
 
-  // warp items, WARP_BATCH per ticket
+  // warp items, WARP_BATCH per ticket.  binary32 (warp_prefetch) prefetches
+  // the next item of the ticket into L2 while the current item runs.
   for (;;) {
     int base = 0;
     if (lane == 0) base = atomicAdd(&a.sc.tickets[1], WARP_BATCH);
@@ -220,6 +241,8 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
         const int64_t vec = Lw[base + j];
         const int64_t s = a.off[vec];
         const int n = (int)(a.off[vec + 1] - s);
+        if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
+          prefetch_item_l2(a, Lw[base + j + 1], lane);
         if (reg_fwd_max<T>() > 0 && n <= reg_fwd_max<T>())  // short: held in registers, read once
           warp_forward<T, 1, (reg_fwd_max<T>() > 0 ? reg_fwd_max<T>() / 32 : 1)>(a.x + s, a.y ? a.y + s : nullptr, n,
                                                                                  lane, a.out, vec);
