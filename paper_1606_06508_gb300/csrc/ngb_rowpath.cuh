@@ -448,6 +448,7 @@ __device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
   const int used = n < CR_SLOTS ? n : CR_SLOTS;
 #pragma unroll
   for (int p = 4; p >= 1; p >>= 1) {
+    if (used <= 32 * p) continue;  // warp-uniform: no slot of chunks p .. 2p-1 holds a term
 #pragma unroll
     for (int i = 0; i < p; ++i)
       if (32 * (i + p) + lane < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
@@ -510,8 +511,10 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
     if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
     Chunk<T, 8, EMU>::squares(v, q);
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 8; ++i) {
+      if (base + 32 * i >= n) break;  // warp-uniform: no additions for chunks past the end
       if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q[i]);
+    }
   }
   return stream_tree<T>(acc, n, lane);
 }
@@ -556,6 +559,7 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
     if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+      if (base + 32 * i >= n) break;  // warp-uniform: no work for chunks past the end
       const int k = base + 32 * i + lane;
       if (k < n) __stcs(yr + k, Chunk<T, 8, EMU>::output(i, h, v[i]));
     }
@@ -910,6 +914,7 @@ __device__ __forceinline__ T bwd_dot_pass(const T* __restrict__ yr, const T* __r
     stream_load8(gr, base, n, lane, b);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+      if (base + 32 * i >= n) break;  // warp-uniform: no work for chunks past the end (acc[i] stays +0, unread)
       T q;
       if constexpr (EMU) {
         ry->take(a[i]);
@@ -947,6 +952,7 @@ __device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T*
     }
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
+      if (base + 32 * i >= n) break;  // warp-uniform: no work for chunks past the end
       const int k = base + 32 * i + lane;
       T p;
       if constexpr (EMU)
