@@ -484,7 +484,7 @@ __device__ __forceinline__ void stream_load8(const T* __restrict__ p, int base, 
 
 // Pass 2 of the forward: the scaled squares in the order CR(n).  SCALED
 // selects x~ = c x; otherwise x~ = x (c = 1).
-template <typename T, bool SCALED, bool EMU>
+template <typename T, bool SCALED, bool EMU, bool TAIL_SKIP = true>
 __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n, int lane, T cf, int E) {
   T acc[8];
 #pragma unroll
@@ -512,7 +512,7 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
     Chunk<T, 8, EMU>::squares(v, q);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      if (base + 32 * i >= n) break;  // warp-uniform: no additions for chunks past the end
+      if (TAIL_SKIP && base + 32 * i >= n) break;  // warp-uniform: no additions for chunks past the end
       if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q[i]);
     }
   }
@@ -660,12 +660,12 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
 
 // Pass 2 for a vector with factor code `code` (not CODE_ZERO); EMU selects
 // the binary64 integer-pipe steps.
-template <typename T, bool EMU>
+template <typename T, bool EMU, bool TAIL_SKIP = true>
 __device__ __forceinline__ T stream_pass2(const T* __restrict__ xr, int n, int lane, int code) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  return code != CODE_ONE ? stream_sum_squares<T, true, EMU>(xr, n, lane, cf, E)
-                          : stream_sum_squares<T, false, EMU>(xr, n, lane, cf, E);
+  return code != CODE_ONE ? stream_sum_squares<T, true, EMU, TAIL_SKIP>(xr, n, lane, cf, E)
+                          : stream_sum_squares<T, false, EMU, TAIL_SKIP>(xr, n, lane, cf, E);
 }
 
 // Pass 3: x^ = h x~.
@@ -693,10 +693,13 @@ __device__ __noinline__ void stream_pass3_slow(const T* __restrict__ xr, T* yr, 
 // Pass 2 and pass 3 of either kind: binary32 always uses the hardware
 // operations inline; binary64 the integer-pipe steps inline when `emu`, the
 // out-of-line hardware passes otherwise.
-template <typename T>
+// TAIL_SKIP: the last, partial round adds only the chunks that hold terms
+// (warp-uniform branches: a gain for short vectors; for the dense binary64
+// rows, which have no partial round, the branches cost 6 % and are left out).
+template <typename T, bool TAIL_SKIP = true>
 __device__ __forceinline__ T stream_pass2_any(const T* __restrict__ xr, int n, int lane, int code, bool emu) {
-  if (sizeof(T) == 4) return stream_pass2<T, false>(xr, n, lane, code);
-  return emu ? stream_pass2<T, true>(xr, n, lane, code) : stream_pass2_slow<T>(xr, n, lane, code);
+  if (sizeof(T) == 4) return stream_pass2<T, false, TAIL_SKIP>(xr, n, lane, code);
+  return emu ? stream_pass2<T, true, TAIL_SKIP>(xr, n, lane, code) : stream_pass2_slow<T>(xr, n, lane, code);
 }
 template <typename T>
 __device__ __forceinline__ void stream_pass3_any(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code,
@@ -769,7 +772,7 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
         code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, sj, have_s);
       }
       if (code != CODE_ZERO) {
-        if (!have_s) sj = stream_pass2_any<T>(xr, n, lane, code, emu);
+        if (!have_s) sj = stream_pass2_any<T, false>(xr, n, lane, code, emu);
         if (lane == j) {
           s = sj;
           code_l = code;
