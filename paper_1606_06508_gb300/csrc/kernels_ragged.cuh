@@ -13,8 +13,9 @@
 //    tickets: whole blocks on block items, warps on batches of warp items,
 //    lanes on thread items.  Warps and blocks stream their vector (three
 //    passes, a few partial sums per lane) instead of holding it, so the
-//    kernel keeps few registers and many loads in flight.  No block ever
-//    waits for another.
+//    kernel keeps few registers and many loads in flight; in binary32 a warp
+//    prefetches its next item into L2 while it works on the current one.  No
+//    block ever waits for another.
 // 3. Backward: one plain grid-stride kernel per list (k_ragged_bwd_blocks,
 //    k_ragged_bwd_warps, k_ragged_bwd_threads).
 // Every mapping evaluates the same operations in the same order (the paper's
@@ -28,25 +29,7 @@ namespace ngb {
 
 constexpr int CLASSIFY_THREADS = 1024;
 constexpr int WARP_BATCH = 4;     // warp items per ticket (binary32 ragged: 4 0.847, 8 0.843, 16 0.825)
-// warp items up to these lengths are held in registers (one read of the
-// vector, the register path of the dense rows); longer ones stream.  0: all
-// stream.  Measured on the ragged workloads: binary64 forward with items up
-// to 256 held 0.31 of the copy bandwidth against 0.40 streaming, up to 128
-// 0.32; binary64 backward up to 128 0.207 against 0.213 (fwd+bwd); binary32
-// forward up to 128 0.805 against 0.798 (within run-to-run noise): all stream.
-constexpr int REG_FWD_F32 = 0, REG_FWD_F64 = 0, REG_BWD_F32 = 0, REG_BWD_F64 = 0;
-template <typename T>
-__host__ __device__ constexpr int reg_fwd_max() { return sizeof(T) == 4 ? REG_FWD_F32 : REG_FWD_F64; }
-template <typename T>
-__host__ __device__ constexpr int reg_bwd_max() { return sizeof(T) == 4 ? REG_BWD_F32 : REG_BWD_F64; }
 constexpr int THREAD_BATCH = 4;   // 32-item groups per ticket
-// binary64 warp items up to this length share one square root and reciprocal
-// per ticket (warp_forward_stream_batch); longer ones are done one by one.
-// 0: no batching.  Measured on the ragged binary64 workload: batching all
-// warp items cuts the FP64 instructions by 15 % but lowers the L1 hit rate
-// (the batch's vectors no longer fit between passes 2 and 3) and runs 3 %
-// slower, so it is off.
-constexpr int F64_BATCH_MAX_LEN = 0;
 
 template <typename T>
 __global__ void __launch_bounds__(CLASSIFY_THREADS)
@@ -232,29 +215,13 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
     if (lane == 0) base = atomicAdd(&a.sc.tickets[1], WARP_BATCH);
     base = __shfl_sync(FULL, base, 0);
     if (base >= nwarp) break;
-    if (sizeof(T) == 8 && F64_BATCH_MAX_LEN > 0) {  // binary64: one square root and reciprocal per batch
-      const int nb = nwarp - base < WARP_BATCH ? nwarp - base : WARP_BATCH;
-      auto item = [&](int j, const T*& xr, T*& yr, int& n, int64_t& vec) {
-        vec = Lw[base + j];
-        const int64_t s = a.off[vec];
-        n = (int)(a.off[vec + 1] - s);
-        xr = a.x + s;
-        yr = a.y ? a.y + s : nullptr;
-      };
-      warp_forward_stream_batch<T, WARP_BATCH, F64_BATCH_MAX_LEN>(item, nb, lane, a.out);
-    } else {
-      for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
-        const int64_t vec = Lw[base + j];
-        const int64_t s = a.off[vec];
-        const int n = (int)(a.off[vec + 1] - s);
-        if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
-          prefetch_item_l2(a, Lw[base + j + 1], lane);
-        if (reg_fwd_max<T>() > 0 && n <= reg_fwd_max<T>())  // short: held in registers, read once
-          warp_forward<T, 1, (reg_fwd_max<T>() > 0 ? reg_fwd_max<T>() / 32 : 1)>(a.x + s, a.y ? a.y + s : nullptr, n,
-                                                                                 lane, a.out, vec);
-        else
-          warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
-      }
+    for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
+      const int64_t vec = Lw[base + j];
+      const int64_t s = a.off[vec];
+      const int n = (int)(a.off[vec + 1] - s);
+      if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
+        prefetch_item_l2(a, Lw[base + j + 1], lane);
+      warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
     }
   }
 
@@ -303,11 +270,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_ragged_bwd_warp
     const int64_t vec = Lw[it];
     const int64_t s = a.off[vec];
     const int n = (int)(a.off[vec + 1] - s);
-    if (reg_bwd_max<T>() > 0 && n <= reg_bwd_max<T>())
-      warp_backward<T, 1, (reg_bwd_max<T>() > 0 ? reg_bwd_max<T>() / 32 : 1)>(a.x + s, a.g + s, a.y + s, n, lane,
-                                                                              a.h_in[vec], a.c_in[vec]);
-    else
-      warp_backward_stream<T>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
+    warp_backward_stream<T>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
   }
 }
 
