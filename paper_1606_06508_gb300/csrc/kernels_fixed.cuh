@@ -327,10 +327,7 @@ cudaError_t launch_warp_rows_bwd(const T* y, const T* g, const T* h, const int8_
 template <typename T>
 cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t count, int dim, bool quat_zero,
                                       cudaStream_t s) {
-  // binary32 rows use 16-byte loads; binary64 rows use 8-byte loads, whose
-  // slot layout needs fewer additions in the summation tree (5 shuffle levels
-  // and 7 in-lane additions instead of 5 x 2 and 7)
-  constexpr int W = sizeof(T) == 4 ? 4 : 1;
+  constexpr int W = 16 / sizeof(T);  // binary32 register rows: 16-byte loads when aligned
   switch (dim) {
     case 1: return launch_small_fwd<T, 1>(x, y, out, count, false, s);
     case 2: return launch_small_fwd<T, 2>(x, y, out, count, false, s);
@@ -344,12 +341,14 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
     k<<<grid, 256, 0, s>>>(x, y, out, count, dim);
     return cudaGetLastError();
   }
-  if (sizeof(T) == 8 && dim <= 16384) {
-    auto k = k_rows_stream_batch<T, F64_ROW_BATCH>;
-    k<<<grid_for(k, 256, (count + F64_ROW_BATCH - 1) / F64_ROW_BATCH, 8), 256, 0, s>>>(x, y, out, count, dim);
-    return cudaGetLastError();
-  }
-  if (dim <= 1024) {
+  if constexpr (sizeof(T) == 8) {  // binary64: streaming warps, 4 rows per warp (integer-pipe steps)
+    if (dim <= 16384) {
+      auto k = k_rows_stream_batch<T, F64_ROW_BATCH>;
+      k<<<grid_for(k, 256, (count + F64_ROW_BATCH - 1) / F64_ROW_BATCH, 8), 256, 0, s>>>(x, y, out, count, dim);
+      return cudaGetLastError();
+    }
+  } else {
+    if (dim <= 1024) {
     if (W > 1 && (dim % W == 0) && aligned16(x) && aligned16(y)) {
       switch (chunks_for(dim, 32 * W)) {
         case 1: return launch_warp_rows<T, W, 1>(x, y, out, count, dim, s);
@@ -367,14 +366,15 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
       case 16: return launch_warp_rows<T, 1, 16>(x, y, out, count, dim, s);
       default: return launch_warp_rows<T, 1, 32>(x, y, out, count, dim, s);
     }
+    }
+    if (dim <= 16384) {
+      auto k = k_rows_stream<T>;
+      k<<<grid_for(k, 256, count, 8), 256, 0, s>>>(x, y, out, count, dim);
+      return cudaGetLastError();
+    }
   }
-  if (dim <= 16384) {
-    auto k = k_rows_stream<T>;
-    k<<<grid_for(k, 256, count, 8), 256, 0, s>>>(x, y, out, count, dim);
-  } else {
-    auto k = k_rows_block<T>;
-    k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
-  }
+  auto k = k_rows_block<T>;
+  k<<<grid_for(k, 256, count, 1), 256, 0, s>>>(x, y, out, count, dim);
   return cudaGetLastError();
 }
 
