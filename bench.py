@@ -354,7 +354,7 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
             L.check(fn(x.data_ptr(), y.data_ptr(), None, None, None, rows, 256, None, None, 0, s.cuda_stream), "rows")
         return Work(desc=f"{rows} rows of 256 {name[-3:]}, forward, N(0,1) x 2^s per row",
                     units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
-                    kernel=('k_rows_warp<float,4,2>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
+                    kernel=('k_rows_half<4>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
                     step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 256, k=2048),
                     bytes_model="2 x 256 x s per row",
                     dp_ops=(3 * rows * 256 + 3 * rows) if dt == torch.float64 else None)

@@ -28,6 +28,8 @@ constexpr int BWD16_IN_FLIGHT = 4;
 // on 2^20 binary32 rows of 256: 1 row 0.887 of the copy bandwidth, 2: 0.861,
 // 3: 0.874, 4: 0.855)
 constexpr int ROWS_IN_FLIGHT = 1;
+// binary32 rows of 129..256 on half-warps (k_rows_half)
+constexpr bool ROWS_HALF_WARP = true;
 
 // ---------------------------------------------------------------------------
 // dim <= 4, one 16-byte vector per thread, U vectors in flight per thread.
@@ -180,6 +182,23 @@ __global__ void __launch_bounds__(256) k_rows_warp(const T* __restrict__ x, T* y
       const int64_t row = row0 + r * nw;
       if (row < count) warp_forward_loaded<T, V, CH>(v[r], x + row * n, y ? y + row * n : nullptr, n, lane, out, row);
     }
+  }
+}
+
+// binary32 rows of 128 < dim <= 256 (multiple of 4, 16-byte aligned): one
+// row per half-warp (half_forward_f32), two rows per warp.
+template <int CH>
+__global__ void __launch_bounds__(256) k_rows_half(const float* __restrict__ x, float* y, VecOut<float> out,
+                                                   int64_t count, int n) {
+  const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15;
+  const unsigned gmask = half ? 0xFFFF0000u : 0x0000FFFFu;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r0 = 2 * w0; r0 < count; r0 += 2 * nw) {
+    const int64_t row = r0 + half;
+    const bool valid = row < count;
+    const int64_t rr = valid ? row : r0;  // the second half of a last, odd pair repeats row r0 without output
+    half_forward_f32<CH>(x + rr * n, (valid && y) ? y + rr * n : nullptr, n, hl, gmask, out, rr, valid);
   }
 }
 
@@ -348,6 +367,11 @@ cudaError_t launch_fixed_forward_impl(const T* x, T* y, VecOut<T> out, int64_t c
       return cudaGetLastError();
     }
   } else {
+    if (ROWS_HALF_WARP && dim > 128 && dim <= 256 && dim % 4 == 0 && aligned16(x) && (!y || aligned16(y))) {
+      auto k = k_rows_half<4>;
+      k<<<grid_for(k, 256, (count + 1) / 2, 8), 256, 0, s>>>(x, y, out, count, dim);
+      return cudaGetLastError();
+    }
     if (dim <= 1024) {
     if (W > 1 && (dim % W == 0) && aligned16(x) && aligned16(y)) {
       switch (chunks_for(dim, 32 * W)) {

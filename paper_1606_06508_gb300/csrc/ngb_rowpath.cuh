@@ -109,6 +109,121 @@ __device__ __forceinline__ T warp_cr_tree(T (&q)[CH][V], int n, int lane) {
   return __shfl_sync(FULL, q[0][0], 0);
 }
 
+// Forward of a binary32 vector of 5 <= n <= 64 CH by one half-warp (16 lanes,
+// gmask names them): lane hl holds the float4 chunks k = 64 c + 4 hl, i.e. the
+// CR slots 64 c + 4 hl + e.  Tree: strides 128 and 64 across the lane's
+// chunks, 32 .. 4 by shuffles inside the half-warp (offsets 8 .. 1), 2 and 1
+// inside the float4.  Two vectors per warp: half the shuffle levels per
+// vector of the 32-lane layout, and twice the loads in flight per warp.
+// xr must be 16-byte aligned and n a multiple of 4.
+template <int CH>
+__device__ __forceinline__ void half_forward_f32(const float* __restrict__ xr, float* yr, int n, int hl,
+                                                 unsigned gmask, const VecOut<float>& out, int64_t vec, bool put) {
+  float v[CH][4];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+    const int k0 = 64 * c + 4 * hl;
+    if (k0 < n) {
+      Vec<float, 4>::load(xr + k0, v[c]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c][e] = 0.0f;
+    }
+  }
+  float m = 0.0f;
+  bool nz = false;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      nz |= !(v[c][e] == 0.0f);
+      m = fmaxf(m, fabsf(v[c][e]));
+    }
+  }
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) m = fmaxf(m, __shfl_xor_sync(gmask, m, o));
+  nz = (__ballot_sync(gmask, nz) & gmask) != 0u;
+  if (!nz) {
+    if (yr) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int k0 = 64 * c + 4 * hl;
+        const float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (k0 < n) Vec<float, 4>::store(yr + k0, z);
+      }
+    }
+    if (put && hl == 0) out.put(vec, 0.0f, 0.0f, CODE_ZERO);
+    return;
+  }
+  const int code = select_code<float, true>(m);
+  const float cf = factor_of<float, true>(code);
+  if (code != CODE_ONE) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[c][e] = __fmul_rn(cf, v[c][e]);
+    }
+  }
+  float q[CH][4];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) q[c][e] = __fmul_rn(v[c][e], v[c][e]);
+  }
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
+  // strides 128 .. 64: chunk c += chunk c + p
+#pragma unroll
+  for (int p = CH / 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int c = 0; c < p; ++c) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (64 * (c + p) + 4 * hl + e < used) q[c][e] = __fadd_rn(q[c][e], q[c + p][e]);
+    }
+  }
+  // strides 32 .. 4: lane hl += lane hl + p (butterfly when every slot holds a term)
+  if (used == 64 * CH && used == CR_SLOTS) {
+#pragma unroll
+    for (int p = 8; p >= 1; p >>= 1) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) q[0][e] = __fadd_rn(q[0][e], __shfl_xor_sync(gmask, q[0][e], p));
+    }
+  } else {
+#pragma unroll
+    for (int p = 8; p >= 1; p >>= 1) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float o = __shfl_xor_sync(gmask, q[0][e], p);
+        if (hl < p && 4 * (hl + p) + e < used) q[0][e] = __fadd_rn(q[0][e], o);
+      }
+    }
+  }
+  // strides 2, 1 inside the float4
+#pragma unroll
+  for (int p = 2; p >= 1; p >>= 1) {
+#pragma unroll
+    for (int e = 0; e < p; ++e)
+      if (e + p < used) q[0][e] = __fadd_rn(q[0][e], q[0][e + p]);
+  }
+  const int src = (int)(__ffs(gmask) - 1);  // lane 0 of the half-warp
+  const float total = (used == CR_SLOTS) ? q[0][0] : __shfl_sync(gmask, q[0][0], src);
+  const float rt = __fsqrt_rn(total);
+  const float h = __frcp_rn(rt);
+  if (yr) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) {
+      const int k0 = 64 * c + 4 * hl;
+      if (k0 < n) {
+        float o[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o[e] = __fmul_rn(h, v[c][e]);
+        Vec<float, 4>::store(yr + k0, o);
+      }
+    }
+  }
+  if (put && hl == 0) out.put(vec, __fmul_rn(inverse_of<float, true>(code), rt), h, code);
+}
+
 // Backward, one warp per vector: dot = CR(y_k g_k), grad_k = ((g_k - y_k dot) h) c.
 template <typename T, int V, int CH>
 __device__ __forceinline__ void warp_backward(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
