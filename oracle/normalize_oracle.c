@@ -98,7 +98,7 @@
 #define INV_SIGMA_MAX_N 0x1p523
 #include "oracle_impl.h"
 
-/* Returns 1 when this build and this thread follow the IEEE model the paper
+/* Returns 1 when the compiled oracle and this thread follow the IEEE model the paper
  * assumes: a product and a sum are rounded separately (no contraction into a
  * fused multiply-add) and subnormal results and operands are kept (no FTZ or
  * DAZ).  The tests refuse to trust the oracle otherwise. */

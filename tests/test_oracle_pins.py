@@ -124,7 +124,7 @@ def test_pythagorean_closed_form(oracle_lib, f):
                 assert float(yk) == exact.round_nearest_even(fr(h) * xk, fmt), (tup, k)
 
 
-def test_survey_closed_form_values(oracle_lib):
+def test_values_show_the_method_is_not_correctly_rounded(oracle_lib):
     """Values that show the method is not correctly rounded (0 ulp is defined
     against the oracle, not against RN(x/r))."""
     y, *_ = oracle_lib.normalize(np.array([3.0, 4.0]), dim=2)
