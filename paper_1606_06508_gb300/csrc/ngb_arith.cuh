@@ -212,8 +212,10 @@ template <> struct Pow2Scale<double> {
 // fallback and no FP64 instruction is issued for these steps.
 // Of every 8 outputs x^_k = h x~_k of a binary64 vector on the integer-pipe
 // path, how many are formed by f64emu::mul (the rest by the FP64 pipe): the
-// two pipes run side by side, and this split balances them.
-constexpr int F64_EMU_OUTPUTS_OF_8 = 4;
+// two pipes run side by side, and this split balances them.  Measured (0 to
+// 8 of 8): ragged binary64 0.40 / 0.42 / 0.43 / 0.42 / 0.41 / 0.34 / 0.33 of
+// the copy bandwidth at 0 / 1 / 2 / 3 / 4 / 6 / 8; dense rows 0.44 at 2 and 4.
+constexpr int F64_EMU_OUTPUTS_OF_8 = 2;
 
 template <typename T, int N, bool EMU> struct Chunk {
   __device__ __forceinline__ static void scale(T c, int /*E*/, T (&v)[N]) {
