@@ -17,7 +17,7 @@ short secondary measurements of the other workloads.
 
 --workload selects another workload of the method for the same JSON line
 (per-workload evidence and profiling): fwdbwd_quat, rows_f32, rows_f64,
-ragged_f32, ragged_f64, fwdbwd_ragged_f64, vec3_f64.
+ragged_f32, ragged_f64, fwdbwd_ragged_f64, vec3_f64, quat_f64.
 
 With N > 1 (torchrun) each rank normalizes its own batch (weak scaling, no
 data exchange); the timing is the max over ranks.
@@ -184,6 +184,9 @@ def host_sample(name: str, n: int):
         dt = np.float32 if name.endswith("f32") else np.float64
         rows = max(1, n // 256)
         return synth.rows(rows, 256, dt, seed=102).reshape(-1), 256, None, rows
+    if name == "quat_f64":
+        x = synth.quaternions_f64(n, seed=105)
+        return x.reshape(-1), 4, None, n
     if name == "vec3_f64":
         x = synth.vectors3_f64(n, seed=103)
         return x.reshape(-1), 3, None, x.shape[0]
@@ -405,6 +408,19 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                     bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector",
                     dp_ops=8 * x.numel() + 3 * cnt)
 
+    if name == "quat_f64":
+        n = count if count != QUAT_COUNT else 1 << 25
+        x = synth.quaternions_f64_torch(n, seed=5 + seed, device=dev)
+        y = torch.empty_like(x)
+
+        def step():
+            L.check(L.normalize_f64(x.data_ptr(), y.data_ptr(), None, None, None, n, 4, None, None, 0,
+                                    s.cuda_stream), "quat_f64")
+        return Work(desc=f"{n} binary64 quaternions (components sign x U[1,2) x 2^e, e in [-30,30]), forward",
+                    units=n, bytes=64 * n, dtype="f64", kernel="k_small_direct<double,4>", launches=1,
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 4),
+                    bytes_model="32 B read + 32 B written per quaternion", dp_ops=15 * n)
+
     if name == "vec3_f64":
         xh = synth.vectors3_f64(65536, seed=0 + seed)
         x = torch.from_numpy(xh).to(dev)
@@ -434,11 +450,12 @@ def full_size_desc(name):
                       "forward, one persistent launch after the classifier",
         "fwdbwd_ragged_f64": "500000 ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
         "vec3_f64": "65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
+        "quat_f64": f"{1 << 25} binary64 quaternions (components sign x U[1,2) x 2^e, e in [-30,30]), forward",
     }[name]
 
 
 WORKLOAD_NAMES = ["quat", "fwdbwd_quat", "rows_f32", "rows_f64", "ragged_f32", "ragged_f64", "fwdbwd_ragged_f64",
-                  "vec3_f64"]
+                  "vec3_f64", "quat_f64"]
 
 
 def paper_tables(torch, L, synth, s):

@@ -100,11 +100,21 @@ __device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr,
     T xv[4], yv[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) xv[k] = k < n ? xr[k] : T(0);
-    switch (n) {
-      case 1: code = normalize_small<T, 1>(xv, yv, r, h, false); break;
-      case 2: code = normalize_small<T, 2>(xv, yv, r, h, false); break;
-      case 3: code = normalize_small<T, 3>(xv, yv, r, h, false); break;
-      default: code = normalize_small<T, 4>(xv, yv, r, h, false); break;
+    bool done = false;
+    if constexpr (sizeof(T) == 8 && SMALL_F64_INTEGER) {  // one integer-pipe form for every n <= 4
+      const SmallKeysF64<4> kk(xv);
+      if (kk.ok) {
+        code = normalize_small_f64_int<4>(xv, yv, r, h, false, kk);
+        done = true;
+      }
+    }
+    if (!done) {
+      switch (n) {
+        case 1: code = normalize_small_hw<T, 1>(xv, yv, r, h, false); break;
+        case 2: code = normalize_small_hw<T, 2>(xv, yv, r, h, false); break;
+        case 3: code = normalize_small_hw<T, 3>(xv, yv, r, h, false); break;
+        default: code = normalize_small_hw<T, 4>(xv, yv, r, h, false); break;
+      }
     }
     if (yr) {
 #pragma unroll

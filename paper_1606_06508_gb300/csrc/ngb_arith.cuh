@@ -59,6 +59,7 @@ template <> struct FP<double> {
   static constexpr double tau_max = 0x1p510, sigma_max = 0x1p-514, inv_sigma_max = 0x1p514;
   static constexpr double tau_max_n = 0x1p501, sigma_max_n = 0x1p-523, inv_sigma_max_n = 0x1p523;
   static constexpr int tau_min_exp = -482, tau_max_n_exp = 501;  // log2 of tau_min, tau_max_n
+  static constexpr int tau_max_exp = 510, sigma_min_exp = 592, sigma_max_exp = -514;  // log2, n <= 4
 };
 
 // The factor choice of Scale2D/Scale3D/Normalize4D: compare the largest
@@ -325,11 +326,11 @@ template <typename T> struct SmallMax<T, 4> {
 };
 
 // Normalize2D / Normalize3D / Normalize4D (Algorithms 5-7; n = 1 runs the same
-// steps on one component).  x and y may be the same array.  quat_zero picks
-// the [0, 0, 1, 0] zero result of Algorithm 7 for D = 4.
-// Returns the factor code; r = sigma r~, h = 1/r~.
+// steps on one component) with the hardware operations.  x and y may be the
+// same array.  quat_zero picks the [0, 0, 1, 0] zero result of Algorithm 7
+// for D = 4.  Returns the factor code; r = sigma r~, h = 1/r~.
 template <typename T, int D>
-__device__ __forceinline__ int normalize_small(const T* x, T* y, T& r, T& h, bool quat_zero) {
+__device__ __forceinline__ int normalize_small_hw(const T* x, T* y, T& r, T& h, bool quat_zero) {
   T m;
   if (SmallMax<T, D>::run(x, m)) {
 #pragma unroll
@@ -353,6 +354,112 @@ __device__ __forceinline__ int normalize_small(const T* x, T* y, T& r, T& h, boo
 #pragma unroll
   for (int k = 0; k < D; ++k) y[k] = FP<T>::mul(h, t[k]);
   return code;
+}
+
+// binary64 vectors of n <= 4 on the integer pipes (Algorithms 5-7 with the
+// operations of f64emu).  Components beyond n are zero: a zero changes
+// neither the largest magnitude nor the sum (s + 0 = s), so one form serves
+// every n <= D.
+//
+// The largest magnitude m and the zero test come from the integer keys of
+// |x_k| (MagTrack<double>::key); tau_min and tau_max are powers of two, so
+// the largest key decides m >= tau_min and m <= tau_max exactly, and for
+// finite components the branch order of Scale2D/Scale3D/Normalize4D only
+// reaches that same maximum.  The form is taken when every component is
+// finite and every nonzero one is normal with |c x_k| >= 2^-511 (keys from
+// (512 - E) << 20 up, c = 2^E); then, with the n <= 4 row of Table 2:
+//   |c x_k| < 2^511 (c = 1: m <= 2^510; sigma_max: m 2^-514 < 2^510;
+//     sigma_min: m 2^592 < 2^110), so every square is normal and below 2^1022
+//     and s <= 4 2^1020 stays finite;
+//   s >= (c m)^2 >= 2^-964 (c = 1: m >= 2^-482; sigma_min: m >= 2^-1022;
+//     sigma_max: m > 2^510), so r~ = sqrt(s) lies in [2^-482, 2^511], 1/r~ is
+//     normal, and h c x_k is 0 or normal (|h| >= 2^-511, |c x_k| >= 2^-511);
+//   r^ = sigma r~ is a power-of-two scaling (f64emu::ldexp_rn: the overflow
+//     to infinity and the subnormal rounding included).
+// c x_k is an exponent addition (exact: x_k and c x_k are normal); the
+// squares, the sum in the order of the algorithms, the square root and the
+// reciprocal are f64emu's correctly rounded operations, and the outputs
+// h c x_k the FP64 pipe's multiplication (SMALL_F64_FP64_OUTPUTS), which
+// runs beside the integer work.  Vectors outside the range take
+// normalize_small_hw.  Measured on 2^25 binary64 quaternions: 1.34 ms with
+// every step on the integer pipes, 1.14 ms with the outputs on the FP64 pipe
+// (3 and 2 components: -17 % and -14 %); the FP64 path alone needs about 95
+// FP64 instructions per quaternion, about 6 ms.
+constexpr bool SMALL_F64_INTEGER = true;
+constexpr bool SMALL_F64_FP64_OUTPUTS = true;
+
+template <int D>
+struct SmallKeysF64 {
+  int code;  // CODE_ZERO for the zero vector
+  int E;     // c = 2^E
+  bool ok;   // the integer-pipe form takes this vector
+  __device__ __forceinline__ explicit SmallKeysF64(const double* x) {
+    constexpr uint32_t HI_INF = 0x7FF00000u;
+    constexpr uint32_t HI_TMIN = (uint32_t)(FP<double>::tau_min_exp + 1023) << 20;
+    constexpr uint32_t HI_TMAX = (uint32_t)(FP<double>::tau_max_exp + 1023) << 20;
+    uint32_t k = 0, kmin1 = 0xFFFFFFFFu;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const uint32_t t = MagTrack<double>::key(x[d]);
+      k = max(k, t);
+      kmin1 = min(kmin1, t - 1u);  // zero components wrap to the top
+    }
+    code = k >= HI_TMIN ? (k <= HI_TMAX ? CODE_ONE : CODE_SIGMA_MAX) : CODE_SIGMA_MIN;
+    E = code == CODE_ONE ? 0 : (code == CODE_SIGMA_MIN ? FP<double>::sigma_min_exp : FP<double>::sigma_max_exp);
+    const int p = 512 - E;
+    const uint32_t tmin = p > 1 ? (uint32_t)p << 20 : (1u << 20);
+    ok = k < HI_INF && kmin1 >= tmin - 1u;
+    if (k == 0u) code = CODE_ZERO;
+  }
+};
+
+template <int D>
+__device__ __forceinline__ int normalize_small_f64_int(const double* x, double* y, double& r, double& h,
+                                                       bool quat_zero, const SmallKeysF64<D>& kk) {
+  if (kk.code == CODE_ZERO) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) y[d] = 0.0;
+    if (D == 4 && quat_zero) y[2] = 1.0;
+    r = 0.0;
+    h = 0.0;
+    return CODE_ZERO;
+  }
+  constexpr uint64_t ABS = 0x7FFFFFFFFFFFFFFFull;
+  const uint64_t shift = (uint64_t)((int64_t)kk.E * (int64_t(1) << 52));
+  uint64_t t[D];
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[d]));
+    t[d] = (b << 1) == 0 ? b : b + shift;  // c (+-0) = +-0
+  }
+  bool finite;  // always true here: s < 2^1023
+  uint64_t s = f64emu::square(t[0] & ABS);
+#pragma unroll
+  for (int d = 1; d < D; ++d) s = f64emu::add_nonneg(s, f64emu::square(t[d] & ABS), finite);
+  const uint64_t rt = f64emu::sqrt_rn(s);
+  const uint64_t hb = f64emu::rcp_rn(rt);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    if (SMALL_F64_FP64_OUTPUTS)
+      y[d] = __dmul_rn(__longlong_as_double(static_cast<long long>(hb)), __longlong_as_double(static_cast<long long>(t[d])));
+    else
+      y[d] = __longlong_as_double(static_cast<long long>(f64emu::mul(t[d], hb)));
+  }
+  r = __longlong_as_double(static_cast<long long>(f64emu::ldexp_rn(rt, -kk.E)));
+  h = __longlong_as_double(static_cast<long long>(hb));
+  return kk.code;
+}
+
+// Normalize2D / Normalize3D / Normalize4D: binary64 vectors in the range of
+// the integer-pipe form take it, every other vector the hardware operations
+// (both give the same bits).
+template <typename T, int D>
+__device__ __forceinline__ int normalize_small(const T* x, T* y, T& r, T& h, bool quat_zero) {
+  if constexpr (sizeof(T) == 8 && SMALL_F64_INTEGER) {
+    const SmallKeysF64<D> kk(x);
+    if (kk.ok) return normalize_small_f64_int<D>(x, y, r, h, quat_zero, kk);
+  }
+  return normalize_small_hw<T, D>(x, y, r, h, quat_zero);
 }
 
 // Backward of y = x/|x| for n <= 4: dot = y.g left to right,

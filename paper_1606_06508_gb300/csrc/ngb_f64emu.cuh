@@ -1,11 +1,12 @@
-// ngb_f64emu.cuh -- binary64 square and sum of non-negative values on the
-// integer pipes.
+// ngb_f64emu.cuh -- binary64 square, product, sum of non-negative values,
+// square root, reciprocal and power-of-two scaling on the integer pipes.
 //
-// The sum of squares of a long vector is a chain of correctly rounded binary64
-// multiplications (x~_k * x~_k) and additions (Eq. 3 evaluated in the order
-// CR(n)).  GB300 executes binary64 arithmetic at a small fraction of its
-// integer rate, so these two operations are rebuilt here from 32-bit integer
-// products, shifts and adds.  Each returns exactly the IEEE 754 result with
+// The sum of squares of a vector is a chain of correctly rounded binary64
+// multiplications (x~_k * x~_k) and additions (Eq. 3 evaluated left to right
+// for n <= 4, in the order CR(n) above), followed by a square root, a
+// reciprocal and the output products (Algorithms 5-7).  GB300 executes
+// binary64 arithmetic at a small fraction of its integer rate, so these
+// operations are rebuilt here from integer products, shifts and adds.  Each returns exactly the IEEE 754 result with
 // round to nearest, ties to even, of the operation it replaces, on the
 // operands it accepts; on any other operand it clears `ok` and the caller
 // uses the hardware instruction instead.  Only the rounding rule of IEEE 754
@@ -16,6 +17,7 @@
 // non-negative (a square or a sum of squares), so the sign bit is zero and
 // the bit patterns of finite values order like the values.
 #pragma once
+#include <math.h>
 #include <stdint.h>
 
 #if defined(__CUDACC__)
@@ -170,6 +172,131 @@ NGB_HD uint64_t add_nonneg(uint64_t a, uint64_t b, bool& ok) {
   const uint64_t sig = round_shift(sum, 10 + c);
   ok = eb <= 2045;
   return ((uint64_t)(uint32_t)(Eb - 1 + c) << 52) + sig;
+}
+
+// High 64 bits of the 128-bit product a b.
+NGB_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+  return __umul64hi(a, b);
+#else
+  return (uint64_t)(((unsigned __int128)a * b) >> 64);
+#endif
+}
+
+// Binary32 reciprocal and reciprocal square root, each within a few units in
+// its last place.  They only start the Newton iterations below, whose exact
+// remainder corrections make the results independent of them.
+NGB_HD float approx_rcp(float f) {
+#if defined(__CUDA_ARCH__)
+  return __frcp_rn(f);
+#else
+  return 1.0f / f;
+#endif
+}
+NGB_HD float approx_rsqrt(float f) {
+#if defined(__CUDA_ARCH__)
+  return rsqrtf(f);
+#else
+  return 1.0f / sqrtf(f);
+#endif
+}
+
+// RN(1 / r) for r > 0 normal with r < 2^1022 (so that 1/r is normal).
+//
+// With r = b 2^(e-1075), b = 2^52 + f: 1/r = (2^105 / b) 2^(970-e), and
+// 2^105 / b lies in (2^52, 2^53] (= 2^53 only for b = 2^52, where 1/r is a
+// power of two).  q = floor(2^105 / b) comes from Newton's iteration
+// x <- x (2 - beta x) for x = 1/beta, beta = b 2^11 / 2^64 in [1/2, 1), in
+// 64-bit fixed point (X = x 2^63), started from a binary32 reciprocal of the
+// top 24 bits of b: two steps take about 22 correct bits to more than 60.
+// Then exactly: the remainder 2^105 - q b is small, so it is computed modulo
+// 2^64, and q is moved until 0 <= remainder < b.  Round to nearest: up when
+// 2 remainder > b; a tie would need b (2q + 1) = 2^106, impossible for q > 0.
+// `start_scale` multiplies the binary32 starting point (1 in use; the host
+// check perturbs it to show that the correction covers a worse start).
+NGB_HD uint64_t rcp_rn(uint64_t r, float start_scale = 1.0f) {
+  const uint32_t e = (uint32_t)(r >> 52);
+  const uint64_t b = (r & FRAC) | (uint64_t(1) << 52);
+  const uint64_t B = b << 11;                          // beta 2^64, in [2^63, 2^64)
+  const float f = (float)(uint32_t)(B >> 40);          // top 24 bits, exact in binary32
+  float x0 = approx_rcp(f) * 0x1p55f * start_scale;    // x 2^31 = X / 2^32
+  x0 = x0 < 4294967295.0f ? x0 : 4294967040.0f;
+  uint64_t X = (uint64_t)(uint32_t)x0 << 32;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t P = mulhi64(B, X);   // beta x 2^63
+    X = mulhi64(X, 0 - P) << 1;         // x (2 - beta x) 2^63
+  }
+  uint64_t q = X >> 11;                              // about 2^105 / b
+  int64_t rem = (int64_t)(0 - q * b);                // 2^105 - q b (2^105 = 0 modulo 2^64)
+#pragma unroll
+  for (int it = 0; it < 3; ++it)
+    if (rem < 0) { q -= 1; rem += (int64_t)b; }
+#pragma unroll
+  for (int it = 0; it < 3; ++it)
+    if (rem >= (int64_t)b) { q += 1; rem -= (int64_t)b; }
+  q += (uint64_t)(2 * rem > (int64_t)b ? 1 : 0);
+  if (b == (uint64_t(1) << 52)) q = uint64_t(1) << 53;  // 1/r is a power of two
+  // q in [2^52, 2^53]: adding it (hidden bit included) to (2044 - e) << 52
+  // gives the biased exponent 2045 - e, or 2046 - e when q = 2^53
+  return ((uint64_t)(2044u - e) << 52) + q;
+}
+
+// RN(sqrt(s)) for s > 0 normal.
+//
+// With s = (m / 2^52) 2^E, m = 2^52 + f: make the exponent even (M = m 2^odd,
+// odd = E mod 2), so that sqrt(s) = sqrt(M 2^52) 2^(Eh - 52), Eh = (E - odd) / 2,
+// and q = floor(sqrt(M 2^52)) lies in [2^52, 2^53).  q comes from Newton's
+// iteration y <- y (3 - mu y^2) / 2 for y = 1/sqrt(mu), mu = M / 2^54 in
+// [1/4, 1), in 64-bit fixed point (Y = y 2^62), started from a binary32
+// reciprocal square root of the top 24 bits of M; then q ~ mu y 2^53.  Then
+// exactly: the remainder M 2^52 - q^2 is small, so it is computed modulo
+// 2^64, and q is moved until 0 <= remainder <= 2q.  Round to nearest: up when
+// remainder > q, since (q + 1/2)^2 = q^2 + q + 1/4; no tie is possible.
+NGB_HD uint64_t sqrt_rn(uint64_t s, float start_scale = 1.0f) {
+  const uint32_t e = (uint32_t)(s >> 52);
+  const uint64_t m = (s & FRAC) | (uint64_t(1) << 52);
+  const int E = (int)e - 1023;
+  const uint32_t odd = (uint32_t)E & 1u;
+  const uint64_t M = m << odd;                         // [2^52, 2^54)
+  const int Eh = (E - (int)odd) / 2;                   // exact: E - odd is even
+  const uint64_t Mq = M << 10;                         // mu 2^64
+  const float f = (float)(uint32_t)(M >> 30);          // top 24 bits, exact in binary32
+  float y0 = approx_rsqrt(f) * 0x1p42f * start_scale;  // y 2^30 = Y / 2^32
+  y0 = y0 < 4294967295.0f ? y0 : 4294967040.0f;
+  uint64_t Y = (uint64_t)(uint32_t)y0 << 32;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const uint64_t Y2 = mulhi64(Y, Y);                 // y^2 2^60
+    const uint64_t T = mulhi64(Mq, Y2);                // mu y^2 2^60
+    const uint64_t D = (uint64_t(3) << 60) - T;        // (3 - mu y^2) 2^60
+    Y = mulhi64(Y, D << 2) << 1;                       // y (3 - mu y^2) / 2 2^62
+  }
+  uint64_t q = mulhi64(Mq, Y) >> 9;                    // mu y 2^53, about sqrt(M 2^52)
+  int64_t rem = (int64_t)((M << 52) - q * q);          // M 2^52 - q^2, modulo 2^64
+#pragma unroll
+  for (int it = 0; it < 3; ++it)
+    if (rem < 0) { rem += (int64_t)(2 * q - 1); q -= 1; }
+#pragma unroll
+  for (int it = 0; it < 3; ++it)
+    if (rem > (int64_t)(2 * q)) { q += 1; rem -= (int64_t)(2 * q - 1); }
+  q += (uint64_t)(rem > (int64_t)q ? 1 : 0);
+  // q in [2^52, 2^53]: the hidden bit (or the carry to 2^53) completes the exponent
+  return ((uint64_t)(uint32_t)(Eh + 1022) << 52) + q;
+}
+
+// RN(a 2^d) for a > 0 normal.  A normal result is exact: the exponent field
+// moves by d.  Above the largest finite value the exact product is at least
+// 2^1024 and rounds to +infinity.  Below 2^-1022 the result counts units of
+// 2^-1074: the significand m (hidden bit included) divided by 2^k,
+// k = 1 - (biased exponent + d), rounded to nearest even; a carry to 2^52
+// gives the smallest normal number by itself.
+NGB_HD uint64_t ldexp_rn(uint64_t a, int d) {
+  const int ne = (int)(a >> 52) + d;
+  if (ne >= 2047) return 0x7FF0000000000000ull;
+  if (ne >= 1) return (uint64_t)((int64_t)a + (int64_t)d * (int64_t(1) << 52));
+  const int k = 1 - ne < 63 ? 1 - ne : 63;
+  return round_shift((a & FRAC) | (uint64_t(1) << 52), k);
 }
 
 }  // namespace f64emu

@@ -94,6 +94,14 @@ def quaternions_f32(count: int, seed: int = 1) -> np.ndarray:
     return np.ascontiguousarray(np.where(pick, wide, normal))
 
 
+def quaternions_f64(count: int, seed: int = 5) -> np.ndarray:
+    """count x 4 binary64 quaternions, each component drawn like those of
+    :func:`vectors3_f64`: random sign x U[1,2) (52 random fraction bits) x 2^e,
+    e uniform in [-30, 30]."""
+    rng = np.random.default_rng(seed)
+    return np.ascontiguousarray(_np_sign_mant_exp(rng, (count, 4), -30, 30, 52))
+
+
 def vectors_f32(count: int, dim: int, seed: int) -> np.ndarray:
     """count x dim binary32 vectors drawn like the quaternion components."""
     rng = np.random.default_rng(seed)
@@ -201,6 +209,18 @@ def quaternions_f32_torch(count: int, seed: int = 1, device="cuda"):
         normal = torch.randn(shp, generator=g, device=device, dtype=torch.float32)
         pick = torch.randint(0, 2, shp, generator=g, device=device, dtype=torch.int32) == 1
         out[a:b] = torch.where(pick, wide, normal)
+    return out
+
+
+def quaternions_f64_torch(count: int, seed: int = 5, device="cuda"):
+    """Device version of :func:`quaternions_f64` (same distribution, chunked)."""
+    torch = _torch()
+    g = _tgen(seed, device)
+    out = torch.empty((count, 4), dtype=torch.float64, device=device)
+    chunk = 1 << 22
+    for a in range(0, count, chunk):
+        b = min(count, a + chunk)
+        out[a:b] = _t_sign_mant_exp(g, (b - a, 4), -30, 30, 52, device)
     return out
 
 

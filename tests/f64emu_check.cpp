@@ -1,5 +1,6 @@
-// Host check of the integer-pipe binary64 square, product and sum (csrc/ngb_f64emu.cuh)
-// against the host's IEEE 754 binary64 multiply and add (round to nearest
+// Host check of the integer-pipe binary64 square, product, sum, square root,
+// reciprocal and power-of-two scaling (csrc/ngb_f64emu.cuh) against the host's
+// IEEE 754 binary64 multiply, add, divide and square root (round to nearest
 // even).  Prints "<cases> <in range> <mismatches>" per operation; any mismatch
 // on an operand the routine takes is a failure.  Built with -ffp-contract=off.
 #include <cmath>
@@ -136,9 +137,65 @@ int main(int argc, char** argv) {
       }
     }
   }
+  // square roots and reciprocals of normal values, with perturbed binary32
+  // starting points (the device's are within a few units of binary32), plus
+  // exact squares and powers of two
+  long sr_cases = 0, sr_bad = 0, rc_cases = 0, rc_bad = 0;
+  const float scales[5] = {1.0f, 1.0f + 0x1p-18f, 1.0f - 0x1p-18f, 1.0f + 0x1p-21f, 1.0f - 0x1p-21f};
+  for (long i = 0; i < n; ++i) {
+    int e = 1 + (int)(next64() % 2046);
+    if (next64() % 4 == 0) e = 1023 + (int)(next64() % 40) - 20;
+    if (next64() % 16 == 0) e = (next64() & 1) ? 1 + (int)(next64() % 3) : 2046 - (int)(next64() % 3);
+    uint64_t a = make(e, (int)(next64() % 6));
+    if (next64() % 8 == 0) {  // an exact square j^2 2^(2t), or its neighbours
+      const uint64_t j = (next64() >> 38) | 1u;  // odd, < 2^26
+      const double sq = (double)j * (double)j;   // exact: < 2^52
+      const int t = (int)(next64() % 800) - 400;
+      a = bits(std::ldexp(sq, 2 * t)) + (uint64_t)((int)(next64() % 3) - 1);
+    }
+    const float sc = scales[next64() % 5];
+    ++sr_cases;
+    const uint64_t r = ngb::f64emu::sqrt_rn(a, sc);
+    if (r != bits(std::sqrt(val(a)))) {
+      if (sr_bad < 5) fprintf(stderr, "sqrt %016llx: %016llx vs %016llx\n", (unsigned long long)a,
+                              (unsigned long long)r, (unsigned long long)bits(std::sqrt(val(a))));
+      ++sr_bad;
+    }
+    if ((a >> 52) <= 2044) {  // r < 2^1022
+      ++rc_cases;
+      const uint64_t h = ngb::f64emu::rcp_rn(a, sc);
+      if (h != bits(1.0 / val(a))) {
+        if (rc_bad < 5) fprintf(stderr, "rcp %016llx: %016llx vs %016llx\n", (unsigned long long)a,
+                                (unsigned long long)h, (unsigned long long)bits(1.0 / val(a)));
+        ++rc_bad;
+      }
+    }
+  }
+  // a 2^d for d in [-1022, 1023] (so that 2^d is a normal binary64 value and
+  // the reference is one IEEE multiplication), results from subnormal to
+  // infinite
+  long ld_bad = 0;
+  for (long i = 0; i < n; ++i) {
+    const int e = 1 + (int)(next64() % 2046);
+    const uint64_t a = make(e, (int)(next64() % 6));
+    int d = (int)(next64() % 2046) - 1022;
+    if (next64() & 1) d = (1 - e) - (int)(next64() % 56) + 2;  // near and below 2^-1022
+    if (d < -1022) d = -1022;
+    if (d > 1023) d = 1023;
+    const uint64_t r = ngb::f64emu::ldexp_rn(a, d);
+    const double ref = val(a) * std::ldexp(1.0, d);
+    if (r != bits(ref)) {
+      if (ld_bad < 5) fprintf(stderr, "ldexp %016llx %d: %016llx vs %016llx\n", (unsigned long long)a, d,
+                              (unsigned long long)r, (unsigned long long)bits(ref));
+      ++ld_bad;
+    }
+  }
+  printf("sqrt %ld %ld %ld\n", n, sr_cases, sr_bad);
+  printf("rcp %ld %ld %ld\n", n, rc_cases, rc_bad);
+  printf("ldexp %ld %ld %ld\n", n, n, ld_bad);
   printf("square %ld %ld %ld\n", n, sq_fast, sq_bad);
   printf("mul_signed %ld %ld %ld\n", n, smul_fast, smul_bad);
   printf("mul %ld %ld %ld\n", n, mul_fast, mul_bad);
   printf("add %ld %ld %ld\n", n, add_fast, add_bad);
-  return (sq_bad || add_bad || mul_bad || smul_bad) ? 1 : 0;
+  return (sq_bad || add_bad || mul_bad || smul_bad || sr_bad || rc_bad || ld_bad) ? 1 : 0;
 }

@@ -59,3 +59,42 @@ def f64_range_edges(count, dim, seed):
             if j % 2:
                 x[i, int(rng.integers(dim))] = -edge[j]
     return x
+
+
+def f64_small_range_edges(count, dim, seed):
+    """binary64 vectors of dim <= 4 at the limits of the integer-pipe form of
+    Normalize2D/3D/4D, whose factor comes from the n <= 4 row of Table 2
+    (tau_min = 2^-482, tau_max = 2^510, sigma_min = 2^592, sigma_max = 2^-514):
+    the smallest nonzero component on, just below or just above |c x| =
+    2^-511; the largest magnitude on and next to tau_min and tau_max; norms
+    r^ = r~ / c at and beyond the overflow threshold; zeros of both signs,
+    subnormals and the smallest normal number."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((count, dim))
+    up = lambda v: np.nextafter(v, np.inf)  # noqa: E731
+    dn = lambda v: np.nextafter(v, 0.0)  # noqa: E731
+    for i in range(count):
+        kind = i % 5
+        edge = []
+        if kind == 0:      # c = 1: max near 1, limit 2^-511
+            edge = [2.0 ** -511, dn(2.0 ** -511), up(2.0 ** -511), 2.0 ** -600, 5e-324, 0.0, -0.0]
+        elif kind == 1:    # sigma_max: max near 2^600, limit 2^3
+            x[i] *= 2.0 ** 600
+            edge = [8.0, dn(8.0), 12.0, 1.0, 2.0 ** -1022, 0.0, -0.0]
+        elif kind == 2:    # sigma_min: max near 2^-500; subnormal components leave the integer form
+            x[i] *= 2.0 ** -500
+            edge = [2.0 ** -1022, dn(2.0 ** -1022), 5e-324, 2.0 ** -700, 0.0, 2.0 ** -1000, -0.0]
+        elif kind == 3:    # the largest magnitude on and next to tau_min and tau_max
+            t = [2.0 ** -482, dn(2.0 ** -482), up(2.0 ** -482), 2.0 ** 510, up(2.0 ** 510),
+                 dn(2.0 ** 510)][(i // 5) % 6]
+            x[i] = t * rng.uniform(0.01, 1.0, size=dim) * np.where(rng.integers(0, 2, size=dim) == 1, -1.0, 1.0)
+            x[i, int(rng.integers(dim))] = t
+        else:              # sigma_max, norms near 2^1024: some overflow to infinity
+            e = rng.integers(1020, 1024, size=dim).astype(np.int32)
+            x[i] = np.ldexp(rng.uniform(1.0, 2.0, size=dim), e) * np.where(rng.integers(0, 2, size=dim) == 1, -1.0, 1.0)
+        j = (i // 5) % (len(edge) + 1)
+        if j < len(edge):  # the last choice leaves the vector untouched
+            x[i, int(rng.integers(dim))] = edge[j]
+            if j % 2:
+                x[i, int(rng.integers(dim))] = -edge[j]
+    return x

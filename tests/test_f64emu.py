@@ -1,6 +1,8 @@
-"""The integer-pipe binary64 square, product and sum (csrc/ngb_f64emu.cuh) against the
-host's IEEE 754 multiply and add, on random and structured operands (ties,
-carries, exponent limits, subnormals, zeros).  The header is plain C++ on the
+"""The integer-pipe binary64 square, product, sum, square root, reciprocal and
+power-of-two scaling (csrc/ngb_f64emu.cuh) against the host's IEEE 754 multiply,
+add, divide and square root, on random and structured operands (ties, carries,
+exponent limits, subnormal results, zeros, exact squares, perturbed Newton
+starting points).  The header is plain C++ on the
 host; the device build uses the same source."""
 import os
 import shutil
@@ -36,3 +38,9 @@ def test_square_and_sum_match_ieee(checker, seed):
     assert bad == 0 and taken > cases // 2
     cases, taken, bad = rows["add"]
     assert bad == 0 and taken > cases // 2
+    cases, taken, bad = rows["sqrt"]
+    assert bad == 0 and taken == cases
+    cases, taken, bad = rows["rcp"]
+    assert bad == 0 and taken > cases * 9 // 10
+    cases, taken, bad = rows["ldexp"]
+    assert bad == 0 and taken == cases

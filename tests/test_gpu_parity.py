@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, cuda_device, f64_range_edges
+from gpu_util import assert_bits, cuda_device, f64_range_edges, f64_small_range_edges
 from paper_1606_06508_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -166,6 +166,23 @@ def test_f64_integer_pipe_limits(dev, dim):
     count = max(36, min(1200, 300000 // dim))
     x = f64_range_edges(count, dim, seed=dim)
     _check_forward(dev, x, dim, what=f"f64 integer-pipe limits d={dim}")
+
+
+@pytest.mark.parametrize("dim", [1, 2, 3, 4])
+def test_small_f64_integer_pipe_limits(dev, dim):
+    """n <= 4 binary64 vectors at the limits of the integer-pipe form (and just
+    outside it), through the 16-byte and the scalar-load kernels."""
+    import torch
+    api = _api()
+    x = f64_small_range_edges(6000 + dim, dim, seed=20 + dim)
+    _check_forward(dev, x, dim, what=f"f64 small limits d={dim}")
+    if dim == 4:
+        _check_forward(dev, x, dim, flags=1, what="f64 small limits d=4 vector semantics")
+    count = x.shape[0]
+    buf = torch.empty(count * dim + 1, dtype=torch.float64, device=dev)
+    buf[1:] = _to(dev, x.reshape(-1))
+    y = api.normalize(buf[1:].view(count, dim))
+    assert_bits(_np(y), oracle.normalize(x.reshape(-1), dim=dim)[0], f"f64 small limits d={dim} misaligned")
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])

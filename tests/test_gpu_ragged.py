@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, cuda_device, f64_range_edges
+from gpu_util import assert_bits, cuda_device, f64_range_edges, f64_small_range_edges
 from paper_1606_06508_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -199,3 +199,34 @@ def test_ragged_f64_integer_pipe_limits(dev):
         assert_bits(_np(y), oy, tag + " y")
         assert_bits(_np(r), orr, tag + " norm")
         assert_bits(_np(c), oc, tag + " code")
+
+
+def test_ragged_small_f64_integer_pipe_limits(dev):
+    """Thread items of lengths 1-4 (one integer-pipe form for every length, the
+    hardware steps per length outside its range) at the limits of
+    gpu_util.f64_small_range_edges, under two mappings, with the backward."""
+    from paper_1606_06508_gb300 import api
+    rng = np.random.default_rng(13)
+    lengths = rng.integers(1, 5, size=12000).astype(np.int64)
+    off = synth.offsets_from_lengths(lengths)
+    pools = {n: f64_small_range_edges(int(np.count_nonzero(lengths == n)), n, seed=30 + n) for n in range(1, 5)}
+    used = {n: 0 for n in range(1, 5)}
+    x = np.empty(int(off[-1]))
+    for i, n in enumerate(lengths):
+        x[off[i]:off[i + 1]] = pools[int(n)][used[int(n)]]
+        used[int(n)] += 1
+    g = rng.standard_normal(x.size)
+    oy, orr, oh, oc = oracle.normalize(x, dim=0, offsets=off)
+    og = oracle.backward(oy, g, oh, oc, dim=0, offsets=off)
+    xt, offt, gt = _to(dev, x), _to(dev, off), _to(dev, g)
+    plan = api.Plan(len(lengths), xt.dtype)
+    for m in ((16, 8192, 256, 0), (4, 1024, 128, 3)):
+        plan.set_mapping(*m)
+        y, r, h, c = api.normalize(xt, offt, return_norm=True, save=True, plan=plan)
+        tag = f"f64 small limits mapping={m}"
+        assert_bits(_np(y), oy, tag + " y")
+        assert_bits(_np(r), orr, tag + " norm")
+        assert_bits(_np(h), oh, tag + " saved_h")
+        assert_bits(_np(c), oc, tag + " code")
+        gr = api.normalize_backward(y, gt, h, c, offt, plan=plan)
+        assert_bits(_np(gr), og, tag + " grad")
