@@ -58,6 +58,12 @@ def rounds_in_sum(n: int) -> int:
     return n if n <= 4 else cr_depth(n)
 
 
+# Lemma 1: |sin phi| <= 1.001 u (n = 2, 3); Lemma 2: |q^_i q^_j - q_i q_j / r^2|
+# <= (1.001 + 8.001 |q_i q_j| / r^2) u.
+SIN_BOUND_U = Fr(1001, 1000)
+PAIR_BOUND_U = (Fr(1001, 1000), Fr(8001, 1000))
+
+
 def direction_bound(n: int, u: Fr) -> Fr:
     """Bound on ||x^ - x/r|| in units of u: (3.001 + n/2) for n <= 4 (Lemmas 1, 2,
     4); for n >= 5 the same proof with n u replaced by the rounding count k of
@@ -133,7 +139,7 @@ def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False, dir_bound_u=None, n
     # Lemma 1: |sin phi| <= 1.001 u for n = 2, 3:  s A - P^2 <= (1.001u)^2 s A
     ok_sin = True
     if n in (2, 3):
-        ok_sin = s * A - P * P <= (Fr(1001, 1000) * u) ** 2 * s * A
+        ok_sin = s * A - P * P <= (SIN_BOUND_U * u) ** 2 * s * A
 
     # norm: finite and within (1 + n/2) r u (+ alpha/2 when 2r <= 3nu/2), claimed
     # when (1 + (1 + n/2) u) r <= omega
@@ -163,7 +169,7 @@ def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False, dir_bound_u=None, n
         for i in range(4):
             for j in range(i, 4):
                 exact = xs[i] * xs[j] / s
-                if abs(ys[i] * ys[j] - exact) > (Fr(1001, 1000) + Fr(8001, 1000) * abs(exact)) * u:
+                if abs(ys[i] * ys[j] - exact) > (PAIR_BOUND_U[0] + PAIR_BOUND_U[1] * abs(exact)) * u:
                     ok_pairs = False
     return Result(n, ok_dir, ok_norm, ok_fin, ok_sin, ok_pairs, err_dir, err_norm)
 
