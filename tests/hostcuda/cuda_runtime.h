@@ -1,51 +1,11 @@
 // Host stand-ins for the CUDA declarations that the per-thread arithmetic of
 // csrc/ngb_arith.cuh uses, so that it compiles with a host C++ compiler for
-// CPU tests (tests/kernel_host_check.cpp).  The __*_rn intrinsics are the
-// host's IEEE 754 operations, round to nearest even (the test builds with
-// -ffp-contract=off, so nothing is fused); bit casts go through memcpy.  The
-// warp collectives are declared for the members of MagTrack that the
-// per-thread paths never call, and act on a single lane.
+// CPU tests (tests/kernel_host_check.cpp).  The arithmetic intrinsics come
+// from ngb_host_intrinsics.h; the warp collectives are declared for the
+// members of MagTrack that the per-thread paths never call, and act on a
+// single lane.
 #pragma once
-#include <math.h>
-#include <stdint.h>
-#include <string.h>
-
-#include <algorithm>
-#include <cmath>
-
-#define __device__
-#define __host__
-#define __forceinline__ inline
-#define __noinline__
-#define __restrict__
-
-using std::max;
-using std::min;
-
-inline float __fmul_rn(float a, float b) { return a * b; }
-inline float __fadd_rn(float a, float b) { return a + b; }
-inline float __fsub_rn(float a, float b) { return a - b; }
-inline float __fdiv_rn(float a, float b) { return a / b; }
-inline float __fsqrt_rn(float a) { return std::sqrt(a); }
-inline float __frcp_rn(float a) { return 1.0f / a; }
-inline double __dmul_rn(double a, double b) { return a * b; }
-inline double __dadd_rn(double a, double b) { return a + b; }
-inline double __dsub_rn(double a, double b) { return a - b; }
-inline double __ddiv_rn(double a, double b) { return a / b; }
-inline double __dsqrt_rn(double a) { return std::sqrt(a); }
-inline double __drcp_rn(double a) { return 1.0 / a; }
-inline float rsqrtf(float a) { return 1.0f / std::sqrt(a); }
-
-inline long long __double_as_longlong(double v) {
-  long long b;
-  memcpy(&b, &v, sizeof b);
-  return b;
-}
-inline double __longlong_as_double(long long b) {
-  double v;
-  memcpy(&v, &b, sizeof v);
-  return v;
-}
+#include "ngb_host_intrinsics.h"
 
 template <typename T>
 inline T __shfl_xor_sync(unsigned, T v, int) { return v; }

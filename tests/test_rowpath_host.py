@@ -1,0 +1,128 @@
+"""The warp and block forms of the kernels' arithmetic (csrc/ngb_rowpath.cuh:
+rows in registers, half-warp rows, streaming warps, 4-row streaming batches,
+streaming blocks, and their backward passes) compiled for the host and run
+on an emulated block of threads (tests/hostwarp/cuda_runtime.h: warp
+collectives and __syncthreads as barriers of std::threads), against the
+oracle, bit for bit, on CPU.  The GPU parity tests check the same code on the
+device; this checks the order CR(n), the streaming passes and the
+integer-pipe binary64 steps without one."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import assert_bits, f64_range_edges
+from paper_1606_06508_gb300 import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(HERE), "paper_1606_06508_gb300", "csrc")
+DT = {"f32": np.float32, "f64": np.float64}
+
+
+@pytest.fixture(scope="module")
+def rph(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no C++ compiler")
+    d = tmp_path_factory.mktemp("rph")
+    exe = str(d / "rowpath_host_check")
+    r = subprocess.run([cxx, "-O2", "-std=c++20", "-ffp-contract=off", "-pthread", "-I",
+                        os.path.join(HERE, "hostwarp"), "-I", CSRC, os.path.join(HERE, "rowpath_host_check.cpp"),
+                        "-o", exe], capture_output=True, text=True)
+    if r.returncode != 0 and "barrier" in r.stderr:
+        pytest.skip("the host C++ library has no <barrier>")
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe, d
+
+
+def _call(rph, f, n, path, parts):
+    exe, d = rph
+    src, dst = str(d / "in.bin"), str(d / "out.bin")
+    with open(src, "wb") as fh:
+        for p in parts:
+            fh.write(np.ascontiguousarray(p).tobytes())
+    subprocess.run([exe, f, str(n), path, src, dst], check=True, timeout=300)
+    return np.fromfile(dst, dtype=np.uint8)
+
+
+def _forward(rph, f, n, path, x, what):
+    dt = DT[f]
+    cnt, s = x.size // n, dt(0).itemsize
+    raw = _call(rph, f, n, path, [x.reshape(-1)])
+    y = raw[: cnt * n * s].view(dt)
+    r = raw[cnt * n * s: (cnt * n + cnt) * s].view(dt)
+    h = raw[(cnt * n + cnt) * s: (cnt * n + 2 * cnt) * s].view(dt)
+    c = raw[(cnt * n + 2 * cnt) * s:].view(np.int8)
+    oy, orr, oh, oc = oracle.normalize(x.reshape(-1), dim=n)
+    assert_bits(y, oy, f"{what} y")
+    assert_bits(r, orr, f"{what} norm")
+    assert_bits(h, oh, f"{what} h")
+    assert_bits(c, oc, f"{what} code")
+
+
+def _backward(rph, f, n, path, x, what):
+    dt = DT[f]
+    oy, _, oh, oc = oracle.normalize(x.reshape(-1), dim=n)
+    g = np.random.default_rng(n).standard_normal(oy.size).astype(dt)
+    raw = _call(rph, f, n, path + "_bwd", [oy, g, oh, oc.astype(np.int8)])
+    assert_bits(raw.view(dt), oracle.backward(oy, g, oh, oc, dim=n), f"{what} grad")
+
+
+def _rows(f, cnt, n, seed):
+    """Rows N(0,1) x 2^s (one s per row over most of the range), with zero
+    rows, NaN, infinities, subnormals and the largest value planted."""
+    dt = DT[f]
+    x = synth.rows(cnt, n, dt, seed=seed)
+    fi = np.finfo(dt)
+    rng = np.random.default_rng(seed)
+    if cnt > 6:
+        x[1] = 0
+        x[2, int(rng.integers(n))] = np.nan
+        x[3, int(rng.integers(n))] = np.inf
+        x[4] = 0
+        x[4, int(rng.integers(n))] = fi.smallest_subnormal
+        x[5, int(rng.integers(n))] = fi.max
+        x[6, : n // 2] = fi.smallest_subnormal * rng.integers(1, 9, n // 2)
+    return x
+
+
+CASES = [  # (dtype, n, path, rows) following the library's dispatch of dense rows
+    ("f32", 17, "warp", 13), ("f32", 33, "warp", 13), ("f32", 100, "warp", 13), ("f32", 255, "warp", 9),
+    ("f32", 256, "warp", 9), ("f32", 257, "warp", 9), ("f32", 1000, "warp", 7), ("f32", 1024, "warp", 7),
+    ("f32", 132, "half", 11), ("f32", 200, "half", 12), ("f32", 252, "half", 9), ("f32", 256, "half", 9),
+    ("f32", 1025, "stream", 9), ("f32", 5000, "stream", 7), ("f32", 16385, "block", 7),
+    ("f64", 17, "batch", 13), ("f64", 100, "batch", 11), ("f64", 256, "batch", 9), ("f64", 1000, "batch", 10),
+    ("f64", 3000, "batch", 9), ("f64", 17, "stream", 9), ("f64", 300, "stream", 9), ("f64", 2048, "stream", 7),
+    ("f64", 16385, "block", 7),
+]
+
+
+@pytest.mark.parametrize("f,n,path,cnt", CASES)
+def test_rows_forward_matches_oracle(rph, f, n, path, cnt):
+    _forward(rph, f, n, path, _rows(f, cnt, n, seed=n + cnt), f"{f} n={n} {path}")
+
+
+@pytest.mark.parametrize("n,path", [(17, "batch"), (256, "batch"), (1000, "batch"), (40, "stream"),
+                                    (3000, "stream"), (20000, "block")])
+def test_f64_rows_integer_pipe_limits(rph, n, path):
+    """binary64 rows whose smallest component sits on, below or above the
+    limits of the integer-pipe steps."""
+    x = f64_range_edges(max(9, min(30, 6000 // n)), n, seed=n)
+    _forward(rph, "f64", n, path, x, f"f64 limits n={n} {path}")
+
+
+@pytest.mark.parametrize("f,n,path", [("f32", 17, "warp"), ("f32", 100, "warp"), ("f32", 1024, "warp"),
+                                      ("f32", 257, "warp"), ("f64", 33, "warp"), ("f64", 1000, "warp"),
+                                      ("f32", 2048, "stream"), ("f64", 1025, "stream"), ("f64", 5000, "stream"),
+                                      ("f32", 16385, "block"), ("f64", 16385, "block")])
+def test_rows_backward_matches_oracle(rph, f, n, path):
+    _backward(rph, f, n, path, _rows(f, 9, n, seed=3 * n), f"{f} n={n} {path}")
+
+
+@pytest.mark.parametrize("n,path", [(40, "warp"), (1025, "stream"), (3000, "stream"), (17000, "block")])
+def test_f64_backward_integer_pipe_limits(rph, n, path):
+    x = f64_range_edges(12, n, seed=2 * n)
+    _backward(rph, "f64", n, path, x, f"f64 limits n={n} {path}")
