@@ -1,0 +1,54 @@
+"""bench.py's host side on CPU: the reference arm (the oracle timed on the
+host cores) prints one JSON line with the benchmark contract's keys for
+every workload, and ranks other than 0 of a multi-rank launch exit without
+work."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+KEYS = ["impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+        "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"]
+
+
+def _bench(args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                          timeout=600, cwd=ROOT, env=e)
+
+
+@pytest.mark.parametrize("name", bench.WORKLOAD_NAMES)
+def test_reference_arm_prints_one_contract_line(name):
+    r = _bench(["--impl", "reference", "--workload", name, "--steps", "3", "--warmup", "3"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert all(k in d for k in KEYS), sorted(set(KEYS) - set(d))
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 3 and d["warmup"] == 3
+    assert d["n_gpus"] == 1 and d["higher_is_better"] is True and d["data"] == "synthetic"
+    assert d["config"]["workload"] == bench.full_size_desc(name)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_other_ranks_exit_without_output():
+    r = _bench(["--impl", "reference", "--steps", "3", "--warmup", "3"],
+               env={"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_every_workload_has_a_full_size_description():
+    for name in bench.WORKLOAD_NAMES:
+        assert bench.full_size_desc(name)
