@@ -174,6 +174,23 @@ def check(x, yhat, rhat, fmt: Fmt, quaternion: bool = False, dir_bound_u=None, n
     return Result(n, ok_dir, ok_norm, ok_fin, ok_sin, ok_pairs, err_dir, err_norm)
 
 
+def check_rows(args):
+    """check() over rows (x, y^, r^), for a process pool: (fmt name, quaternion,
+    xs, ys, rs) -> indices of the rows that fail, and the worst direction error
+    in units of u.  Zero rows are skipped."""
+    fmt_name, quaternion, xs, ys, rs = args
+    fmt = F32 if fmt_name == "f32" else F64
+    bad, worst = [], 0.0
+    for i in range(len(xs)):
+        if not np.any(xs[i] != 0):
+            continue
+        res = check(xs[i], ys[i], rs[i], fmt, quaternion=quaternion)
+        if not res.ok:
+            bad.append(i)
+        worst = max(worst, res.err_direction_u)
+    return bad, worst
+
+
 def exact_gradient(x, g):
     """(g - x^ (x^ . g)) / r with x^ = x / r, as Fractions except for the one
     square root, carried to 256 bits.  Returns floats."""

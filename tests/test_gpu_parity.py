@@ -81,6 +81,15 @@ def test_small_dims(dev, f, dim):
         _check_forward(dev, x, dim, flags=1, what=f"{f} d=4 vector semantics")
 
 
+def test_full_exponent_grid_two_components_f32(dev):
+    """n = 2, binary32: every exponent pair in [-149, 127]^2, the mantissas
+    {1, 1.5, 2 - 2^-23} for each component and the four sign patterns."""
+    from test_oracle_pins import full_grid_two_f32
+    x = full_grid_two_f32(signs=(1.0, -1.0))
+    x = np.concatenate([x, -x])
+    _check_forward(dev, x, 2, what="f32 n=2 full exponent grid")
+
+
 def test_quaternions_config_recipe(dev):
     x = synth.quaternions_f32(200003, seed=1)
     _check_forward(dev, x, 4, what="quaternions")

@@ -99,6 +99,17 @@ def test_small_forward_matches_oracle(khc, f, dim):
             _check_forward(khc, x, dim, "fwd", flags=1, what=f"{f} d=4 set {k} vector semantics")
 
 
+def test_full_exponent_grid_two_components_f32(khc):
+    """n = 2, binary32: every exponent pair in [-149, 127]^2, the mantissas
+    {1, 1.5, 2 - 2^-23} for each component and the four sign patterns
+    (2,762,244 vectors), bit for bit."""
+    from test_oracle_pins import full_grid_two_f32
+    x = full_grid_two_f32(signs=(1.0, -1.0))
+    x = np.concatenate([x, -x])
+    assert x.shape == (4 * 277 * 277 * 9, 2)
+    _check_forward(khc, x, 2, "fwd", what="f32 n=2 full exponent grid")
+
+
 def test_config0_vectors_take_the_integer_form(khc):
     """The 65,600 x 3 binary64 case through the library's forward."""
     x = synth.vectors3_f64(65536, seed=0)

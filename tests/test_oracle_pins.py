@@ -14,6 +14,7 @@ The oracle is the sequence of IEEE operations of Algorithms 3-7 of arXiv
 """
 from fractions import Fraction as Fr
 import math
+import os
 
 import numpy as np
 import pytest
@@ -325,6 +326,34 @@ def test_bounds_brute_force_two_components(oracle_lib, f):
             vals.append((math.ldexp(m1, e1), s2 * math.ldexp(m2, e2)))
     x = np.array(vals, dtype=np.float64).astype(dt)
     _bound_sweep(oracle_lib, x, 2, f)
+
+
+def full_grid_two_f32(signs=(1.0,)):
+    """Every exponent pair (e1, e2) in [-149, 127]^2 of binary32, with the
+    mantissas {1, 1.5, 2 - 2^-23} for each component and the sign patterns of
+    x2 (x1's sign is covered by the sign-flip invariance)."""
+    es = np.arange(-149, 128)
+    mants = np.array([1.0, 1.5, 2.0 - 2.0 ** -23])
+    e1, e2, m1, m2, sg = np.meshgrid(es, es, mants, mants, np.array(signs), indexing="ij")
+    x1 = np.ldexp(m1, e1).reshape(-1)
+    x2 = (sg * np.ldexp(m2, e2)).reshape(-1)
+    return np.stack([x1, x2], axis=1).astype(np.float32)
+
+
+def test_bounds_full_exponent_grid_two_components_f32(oracle_lib):
+    """n = 2, binary32: the whole exponent grid (690,561 vectors) within the
+    bounds of Lemma 1, decided in exact arithmetic on all host cores."""
+    import multiprocessing as mp
+    x = full_grid_two_f32()
+    assert x.shape == (277 * 277 * 9, 2)
+    y, r, _, _ = oracle_lib.normalize(x.reshape(-1), dim=2)
+    y = y.reshape(-1, 2)
+    chunks = [(a, min(a + 20000, x.shape[0])) for a in range(0, x.shape[0], 20000)]
+    with mp.get_context("spawn").Pool(min(len(chunks), os.cpu_count() or 1)) as pool:
+        res = pool.map(exact.check_rows, [("f32", False, x[a:b], y[a:b], r[a:b]) for a, b in chunks])
+    bad = [a + i for (a, _), (b_, _) in zip(chunks, res) for i in b_]
+    assert not bad, [x[i].tolist() for i in bad[:5]]
+    assert max(w for _, w in res) <= 4.001
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])
