@@ -340,20 +340,36 @@ def full_grid_two_f32(signs=(1.0,)):
     return np.stack([x1, x2], axis=1).astype(np.float32)
 
 
+def _bounds_on_all_cores(oracle_lib, x, n, f, quaternion=False, chunk=20000):
+    """The oracle's outputs for the rows of x within the paper's bounds, decided
+    by exact.check on a spawn pool over the host cores; returns the worst
+    direction error in units of u."""
+    import multiprocessing as mp
+    y, r, _, _ = oracle_lib.normalize(x.reshape(-1), dim=n)
+    y = y.reshape(-1, n)
+    chunks = [(a, min(a + chunk, x.shape[0])) for a in range(0, x.shape[0], chunk)]
+    with mp.get_context("spawn").Pool(min(len(chunks), os.cpu_count() or 1)) as pool:
+        res = pool.map(exact.check_rows, [(f, quaternion, x[a:b], y[a:b], r[a:b]) for a, b in chunks])
+    bad = [a + i for (a, _), (failed, _) in zip(chunks, res) for i in failed]
+    assert not bad, [x[i].tolist() for i in bad[:5]]
+    return max(w for _, w in res)
+
+
 def test_bounds_full_exponent_grid_two_components_f32(oracle_lib):
     """n = 2, binary32: the whole exponent grid (690,561 vectors) within the
-    bounds of Lemma 1, decided in exact arithmetic on all host cores."""
-    import multiprocessing as mp
+    bounds of Lemma 1."""
     x = full_grid_two_f32()
     assert x.shape == (277 * 277 * 9, 2)
-    y, r, _, _ = oracle_lib.normalize(x.reshape(-1), dim=2)
-    y = y.reshape(-1, 2)
-    chunks = [(a, min(a + 20000, x.shape[0])) for a in range(0, x.shape[0], 20000)]
-    with mp.get_context("spawn").Pool(min(len(chunks), os.cpu_count() or 1)) as pool:
-        res = pool.map(exact.check_rows, [("f32", False, x[a:b], y[a:b], r[a:b]) for a, b in chunks])
-    bad = [a + i for (a, _), (b_, _) in zip(chunks, res) for i in b_]
-    assert not bad, [x[i].tolist() for i in bad[:5]]
-    assert max(w for _, w in res) <= 4.001
+    assert _bounds_on_all_cores(oracle_lib, x, 2, "f32") <= 4.001
+
+
+def test_bounds_whole_config0_and_sampled_quaternions(oracle_lib):
+    """Every vector of the 65,600 x 3 binary64 case (Lemma 1), and 200,000
+    binary32 quaternions of the headline recipe (Lemma 2, with the products
+    q^_i q^_j)."""
+    _bounds_on_all_cores(oracle_lib, synth.vectors3_f64(65536, seed=0), 3, "f64", chunk=5000)
+    _bounds_on_all_cores(oracle_lib, synth.quaternions_f32(200000, seed=11), 4, "f32", quaternion=True,
+                         chunk=5000)
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])
