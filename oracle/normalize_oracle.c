@@ -33,9 +33,11 @@
  *   - the backward pass (no counterpart in the paper) is
  *     grad = ((g - y (y.g)) * h) * c.
  *
- * Parity of the n >= 5 summation order and of the backward operation order
- * is pinned by the error bounds and invariants checked in the tests, not by
- * the paper, which does not define them.
+ * Parity unpinned: the n >= 5 summation order CR(n) and the backward
+ * operation order are this project's definitions (the paper defines
+ * neither).  The tests pin them only by the error bounds, invariants, exact
+ * integer norms, finite differences and the exact gradient, which another
+ * order within the bounds would pass as well.
  */
 #include <math.h>
 #include <stdint.h>
