@@ -1,5 +1,6 @@
-"""Helpers for the GPU parity tests: bitwise comparison with NaN as a class,
-and binary64 inputs at the limits of the integer-pipe steps."""
+"""Helpers for the parity tests (GPU and host builds): bitwise comparison with
+NaN as a class, binary64 inputs at the limits of the integer-pipe steps, and
+the two-component binary32 exponent grid."""
 import numpy as np
 import pytest
 
@@ -98,3 +99,15 @@ def f64_small_range_edges(count, dim, seed):
             if j % 2:
                 x[i, int(rng.integers(dim))] = -edge[j]
     return x
+
+
+def full_grid_two_f32(signs=(1.0,)):
+    """Every exponent pair (e1, e2) in [-149, 127]^2 of binary32, with the
+    mantissas {1, 1.5, 2 - 2^-23} for each component and the sign patterns of
+    x2 (x1's sign is covered by the sign-flip invariance)."""
+    es = np.arange(-149, 128)
+    mants = np.array([1.0, 1.5, 2.0 - 2.0 ** -23])
+    e1, e2, m1, m2, sg = np.meshgrid(es, es, mants, mants, np.array(signs), indexing="ij")
+    x1 = np.ldexp(m1, e1).reshape(-1)
+    x2 = (sg * np.ldexp(m2, e2)).reshape(-1)
+    return np.stack([x1, x2], axis=1).astype(np.float32)

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, cuda_device, f64_range_edges, f64_small_range_edges
+from gpu_util import assert_bits, cuda_device, f64_range_edges, f64_small_range_edges, full_grid_two_f32
 from paper_1606_06508_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -84,7 +84,6 @@ def test_small_dims(dev, f, dim):
 def test_full_exponent_grid_two_components_f32(dev):
     """n = 2, binary32: every exponent pair in [-149, 127]^2, the mantissas
     {1, 1.5, 2 - 2^-23} for each component and the four sign patterns."""
-    from test_oracle_pins import full_grid_two_f32
     x = full_grid_two_f32(signs=(1.0, -1.0))
     x = np.concatenate([x, -x])
     _check_forward(dev, x, 2, what="f32 n=2 full exponent grid")

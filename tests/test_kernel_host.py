@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import assert_bits, f64_small_range_edges
+from gpu_util import assert_bits, f64_small_range_edges, full_grid_two_f32
 from paper_1606_06508_gb300 import synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -103,7 +103,6 @@ def test_full_exponent_grid_two_components_f32(khc):
     """n = 2, binary32: every exponent pair in [-149, 127]^2, the mantissas
     {1, 1.5, 2 - 2^-23} for each component and the four sign patterns
     (2,762,244 vectors), bit for bit."""
-    from test_oracle_pins import full_grid_two_f32
     x = full_grid_two_f32(signs=(1.0, -1.0))
     x = np.concatenate([x, -x])
     assert x.shape == (4 * 277 * 277 * 9, 2)

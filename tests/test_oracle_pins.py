@@ -20,6 +20,7 @@ import numpy as np
 import pytest
 
 import exact
+from gpu_util import full_grid_two_f32
 from exact import F32, F64, fr
 from paper_1606_06508_gb300 import synth
 
@@ -326,18 +327,6 @@ def test_bounds_brute_force_two_components(oracle_lib, f):
             vals.append((math.ldexp(m1, e1), s2 * math.ldexp(m2, e2)))
     x = np.array(vals, dtype=np.float64).astype(dt)
     _bound_sweep(oracle_lib, x, 2, f)
-
-
-def full_grid_two_f32(signs=(1.0,)):
-    """Every exponent pair (e1, e2) in [-149, 127]^2 of binary32, with the
-    mantissas {1, 1.5, 2 - 2^-23} for each component and the sign patterns of
-    x2 (x1's sign is covered by the sign-flip invariance)."""
-    es = np.arange(-149, 128)
-    mants = np.array([1.0, 1.5, 2.0 - 2.0 ** -23])
-    e1, e2, m1, m2, sg = np.meshgrid(es, es, mants, mants, np.array(signs), indexing="ij")
-    x1 = np.ldexp(m1, e1).reshape(-1)
-    x2 = (sg * np.ldexp(m2, e2)).reshape(-1)
-    return np.stack([x1, x2], axis=1).astype(np.float32)
 
 
 def _bounds_on_all_cores(oracle_lib, x, n, f, quaternion=False, chunk=20000):
