@@ -197,24 +197,36 @@ def host_sample(name: str, n: int):
     return synth.ragged_values(lengths, dt, seed=104), 0, synth.offsets_from_lengths(lengths), cnt
 
 
-def cpu_baseline(name: str, seconds: float = 10.0):
+def cpu_baseline(name: str, seconds: float = 10.0, single_seconds: float = 3.0):
     """The oracle as it stands, on all host cores over contiguous vector ranges,
-    repeated on a bounded sample of the workload for about `seconds`."""
+    repeated on a bounded sample of the workload for about `seconds`; then the
+    same on one thread for about `single_seconds`.  Vectors/s and GB/s (input
+    and output values once, plus offsets) for both."""
     import oracle
     oracle.build()
     threads = cpu_threads()
     x, dim, off, units = host_sample(name, 1 << 21)
-    oracle.normalize_threads(x, dim, off, threads=threads)
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        oracle.normalize_threads(x, dim, off, threads=threads)
-        reps += 1
-        dt = time.perf_counter() - t0
-        if dt > seconds or reps >= 100000:
-            break
+    nbytes = 2 * x.nbytes + (off.nbytes if off is not None else 0)
+
+    def timed(nthreads, budget):
+        oracle.normalize_threads(x, dim, off, threads=nthreads)
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            oracle.normalize_threads(x, dim, off, threads=nthreads)
+            reps += 1
+            dt = time.perf_counter() - t0
+            if dt > budget or reps >= 100000:
+                return reps, dt
+
+    reps, dt = timed(threads, seconds)
+    reps1, dt1 = timed(1, single_seconds)
     return {"value": reps * units / dt, "unit": "vectors/s", "cores": threads, "kind": "oracle",
+            "GB_per_s": reps * nbytes / dt / 1e9,
             "sample": f"{reps} x {units} vectors of the same recipe ({dt:.1f} s, forward), oracle on {threads} "
-                      "host threads over contiguous vector ranges"}
+                      "host threads over contiguous vector ranges",
+            "single_thread": {"value": reps1 * units / dt1, "unit": "vectors/s", "cores": 1,
+                              "GB_per_s": reps1 * nbytes / dt1 / 1e9,
+                              "sample": f"{reps1} x {units} vectors ({dt1:.1f} s), oracle on one thread"}}
 
 
 # ---------------------------------------------------------------------------- parity of the timed outputs

@@ -52,3 +52,12 @@ def test_reference_arm_other_ranks_exit_without_output():
 def test_every_workload_has_a_full_size_description():
     for name in bench.WORKLOAD_NAMES:
         assert bench.full_size_desc(name)
+
+
+@pytest.mark.parametrize("name", ["quat", "ragged_f64"])
+def test_cpu_baseline_reports_all_cores_and_one_thread(name):
+    cb = bench.cpu_baseline(name, seconds=0.5, single_seconds=0.5)
+    assert cb["kind"] == "oracle" and cb["unit"] == "vectors/s" and cb["value"] > 0 and cb["GB_per_s"] > 0
+    assert cb["cores"] == bench.cpu_threads()
+    st = cb["single_thread"]
+    assert st["cores"] == 1 and st["value"] > 0 and st["GB_per_s"] > 0
