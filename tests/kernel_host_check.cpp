@@ -12,6 +12,8 @@
 //   padded  binary64: the components zero-padded to 4 and the integer-pipe
 //           form for n <= 4 when in range, else normalize_small_hw (the
 //           ragged kernel's thread items)
+//   quot1, quot2  dim 3: the quotient Algorithms 1 and 2 (ngb_quotient.cuh);
+//           h and code are written as zero
 // Mode bwd reads y, g (count x dim each), h (count) and code (count bytes)
 // and writes grad (count x dim): backward_small or backward_thread_generic.
 #include <cstdio>
@@ -20,6 +22,7 @@
 #include <vector>
 
 #include "ngb_arith.cuh"
+#include "ngb_quotient.cuh"
 
 using namespace ngb;
 
@@ -32,6 +35,19 @@ static std::vector<T> read_vals(FILE* f, size_t n) {
 
 template <typename T, int D>
 static int fwd_small(const T* x, T* y, T& r, T& h, bool qz, const char* mode) {
+  if (!strcmp(mode, "quot1") || !strcmp(mode, "quot2")) {
+    if constexpr (D == 3) {
+      const T xv[3] = {x[0], x[1], x[2]};
+      T yv[3];
+      if (mode[4] == '1') quotient1_3<T>(xv, yv, r);
+      else quotient2_3<T>(xv, yv, r);
+      for (int k = 0; k < 3; ++k) y[k] = yv[k];
+      h = T(0);
+      return 0;
+    }
+    fprintf(stderr, "the quotient modes take dim 3\n");
+    exit(2);
+  }
   if (!strcmp(mode, "hw")) return normalize_small_hw<T, D>(x, y, r, h, qz);
   if (!strcmp(mode, "padded")) {
     if constexpr (sizeof(T) == 8) {

@@ -3,7 +3,7 @@ through tests/kernel_host_check.cpp, the CUDA intrinsics mapped to the host's
 IEEE operations by tests/hostcuda/cuda_runtime.h) against the oracle, bit for
 bit, on CPU: the n <= 4 forward in its integer-pipe and hardware forms, the
 zero-padded form of the ragged thread items, the generic thread path for
-5 <= n <= 16 and the backward.  The GPU parity tests check the same code on
+5 <= n <= 16, the backward, and the quotient Algorithms 1 and 2.  The GPU parity tests check the same code on
 the device; this catches a mistake in the arithmetic without one."""
 import os
 import shutil
@@ -107,6 +107,18 @@ def test_full_exponent_grid_two_components_f32(khc):
     x = np.concatenate([x, -x])
     assert x.shape == (4 * 277 * 277 * 9, 2)
     _check_forward(khc, x, 2, "fwd", what="f32 n=2 full exponent grid")
+
+
+@pytest.mark.parametrize("f", ["f32", "f64"])
+@pytest.mark.parametrize("alg", [1, 2])
+def test_quotient_algorithms_match_oracle(khc, f, alg):
+    """The quotient Algorithms 1 and 2 of the comparison kernels (y and r)."""
+    rng = np.random.default_rng(alg)
+    x = _specials(synth.vectors_f32(20000, 3, seed=alg) if f == "f32" else synth.vectors_f64(20000, 3, seed=alg), rng)
+    y, r, _, _ = _forward(khc, x, 3, f"quot{alg}")
+    oy, orr = oracle.quotient3(x, alg)
+    assert_bits(y, oy.reshape(-1), f"{f} Algorithm {alg} y")
+    assert_bits(r, orr, f"{f} Algorithm {alg} r")
 
 
 def test_config0_vectors_take_the_integer_form(khc):
