@@ -364,15 +364,20 @@ def test_bounds_whole_config0_and_sampled_quaternions(oracle_lib):
 @pytest.mark.parametrize("f", ["f32", "f64"])
 @pytest.mark.parametrize("n", [3, 4])
 def test_bounds_one_and_two_nonzero(oracle_lib, f, n):
+    """Every placement of one or two nonzero components, each with 200 random
+    exponents from the whole range (subnormals included) and random signs."""
+    import itertools
     dt = DT[f]
     rng = np.random.default_rng(31 + n)
     emin, emax = (-149, 127) if f == "f32" else (-1074, 1023)
     xs = []
-    for _ in range(1500):
-        x = np.zeros(n)
-        k = rng.choice(n, size=rng.integers(1, 3), replace=False)
-        x[k] = np.ldexp(rng.uniform(1, 2, len(k)), rng.integers(emin, emax + 1, len(k)))
-        xs.append(x)
+    for size in (1, 2):
+        for pos in itertools.combinations(range(n), size):
+            for _ in range(200):
+                x = np.zeros(n)
+                sign = np.where(rng.integers(0, 2, size) == 1, -1.0, 1.0)
+                x[list(pos)] = sign * np.ldexp(rng.uniform(1, 2, size), rng.integers(emin, emax + 1, size))
+                xs.append(x)
     _bound_sweep(oracle_lib, np.array(xs).astype(dt), n, f, flags=1)
 
 
