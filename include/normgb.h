@@ -13,7 +13,7 @@
  *   y_k = h x~_k  (the normalized vector x/|x|) and r = c^{-1} r~  (its norm)
  *                                                   (Algs. 5, 6, 7; Eqs. (1), (2)).
  * n <= 4 follows the printed algorithms (left-to-right sums); n >= 5 sums in
- * a fixed canonical order (1024 slots and a halving tree) with
+ * a fixed canonical order (256 slots and a halving tree) with
  * tau_max = 2^53 (binary32) or 2^501 (binary64) so that up to 2^20 squares
  * cannot overflow.  Every kernel mapping (thread, warp or block per vector)
  * returns the same bits, and they equal a sequential evaluation of the same
@@ -84,7 +84,15 @@ typedef enum ngb_status {
  * Dense dim == 4 uses the quaternion zero result (0, 0, 1, 0) of Algorithm 7
  * unless NGB_VECTOR_SEMANTICS is set; ragged vectors always use the vector
  * rule.  A NaN component makes every output of its vector NaN.
- * Returns NGB_OK once the work is queued.
+ * Ragged x (and y) may be NULL when the batch has no elements
+ * (offsets[count] == offsets[0], e.g. a zero-element tensor): the empty
+ * vectors are finished as usual, and a vector of positive length in such a
+ * call is skipped and reported as bad offsets (nothing is read through the
+ * NULL pointer).  A dense call with count > 0 needs x.
+ * Returns NGB_OK once the work is queued; NGB_ERR_INVALID_ARG (negative
+ * count or dim, unknown flag, offsets given for a dense batch or missing for
+ * a ragged one, NULL x for a dense batch), NGB_ERR_UNSUPPORTED (dim >
+ * NGB_MAX_LEN, ragged count >= 2^31), NGB_ERR_NO_PLAN, NGB_ERR_CUDA.
  */
 ngb_status normalize_f32(const float* x, float* y, float* norm, float* saved_h, int8_t* saved_code, int64_t count,
                          int32_t dim, const int64_t* offsets, ngb_plan* plan, uint32_t flags, ngb_stream_t stream);
@@ -99,7 +107,10 @@ ngb_status normalize_f64(const double* x, double* y, double* norm, double* saved
  *   n <= 4, the canonical order for n >= 5), grad_k = ((g_k - y_k dot) h) c,
  * from the forward's y, saved_h and saved_code, so x is not read again.
  * grad = +0 for a zero input vector.  grad may equal g.  Same layout, count,
- * dim, offsets and plan rules as the forward call.
+ * dim, offsets and plan rules as the forward call.  saved_h and saved_code
+ * are required when count > 0; y, g and grad are required for a dense batch
+ * and, for a ragged batch, may be NULL only when it has no elements (as for
+ * the forward call: vectors of positive length are then skipped and reported).
  */
 ngb_status normalize_backward_f32(const float* y, const float* g, const float* saved_h, const int8_t* saved_code,
                                   float* grad, int64_t count, int32_t dim, const int64_t* offsets, ngb_plan* plan,
@@ -224,7 +235,12 @@ ngb_status ngb_fp64_probe(double* out, int32_t blocks, int32_t iters, int64_t* f
  * Every call shares the array and clears its counters on `stream` before
  * use, so calls that overlap on the GPU (two streams, or two threads with
  * different streams) race and must be serialized by the caller.  Vectors
- * with bad offsets are skipped (there is no plan to report them); results
+ * with a negative length, a length above NGB_MAX_LEN, a negative start or
+ * (with NGB_VALIDATE_OFFSETS) offsets[0] != 0 are skipped, and nothing
+ * reports that they were: there is no plan status word to read.  An end
+ * offset past the caller's x buffer is NOT detected on this path (there is no
+ * capacity argument); the caller must pass offsets that stay inside x.  x and
+ * y may be NULL for a batch without elements, as for normalize_f32.  Results
  * are bit-identical to normalize_f32 with a plan.  No cudaMalloc, cudaFree
  * or allocating library routine is called.
  * x, y, norm, saved_h, saved_code, count, offsets: as normalize_f32 (dim == 0);

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "normgb.h"
+#include "ngb_args.h"
 #include "ngb_internal.h"
 
 namespace {
@@ -83,11 +84,13 @@ ngb_status check_plan(ngb_plan* plan, int64_t count, int dtype_bytes) {
 
 template <typename T>
 ngb_status run_ragged(ngb_plan* p, const T* x, T* y, T* norm, T* h, int8_t* code, const T* g, const T* h_in,
-                      const int8_t* c_in, T* grad, const int64_t* off, bool validate, bool bwd, cudaStream_t s) {
+                      const int8_t* c_in, T* grad, const int64_t* off, bool validate, bool bwd, bool no_elements,
+                      cudaStream_t s) {
   ngb::RaggedMapping m = p->map;
+  const int64_t capacity = ngb::classifier_capacity(p->capacity, no_elements);
   if (m.grid_blocks <= 0) m.grid_blocks = ngb::ragged_full_wave<T>(m, bwd);
   if (!p->graphs || stream_capturing(s)) {
-    cudaError_t e = ngb::launch_ragged<T>(x, y, norm, h, code, g, h_in, c_in, grad, off, p->count, p->capacity,
+    cudaError_t e = ngb::launch_ragged<T>(x, y, norm, h, code, g, h_in, c_in, grad, off, p->count, capacity,
                                           validate, m, p->sc, bwd, s);
     return e == cudaSuccess ? NGB_OK : cuda_fail(e, "ragged launch");
   }
@@ -109,7 +112,7 @@ ngb_status run_ragged(ngb_plan* p, const T* x, T* y, T* norm, T* h, int8_t* code
     }
     cudaError_t e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    cudaError_t le = ngb::launch_ragged<T>(x, y, norm, h, code, g, h_in, c_in, grad, off, p->count, p->capacity,
+    cudaError_t le = ngb::launch_ragged<T>(x, y, norm, h, code, g, h_in, c_in, grad, off, p->count, capacity,
                                            validate, m, p->sc, bwd, p->cap_stream);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(p->cap_stream, &graph);
@@ -134,51 +137,39 @@ template <typename T>
 ngb_status forward(const T* x, T* y, T* norm, T* h, int8_t* code, int64_t count, int32_t dim, const int64_t* off,
                    ngb_plan* plan, uint32_t flags, ngb_stream_t stream) {
   g_last_error.clear();
-  if (count < 0) return fail(NGB_ERR_INVALID_ARG, "count < 0");
-  if (dim < 0) return fail(NGB_ERR_INVALID_ARG, "dim < 0");
-  if (dim > NGB_MAX_LEN) return fail(NGB_ERR_UNSUPPORTED, "dim > NGB_MAX_LEN");
-  if (flags & ~(NGB_VECTOR_SEMANTICS | NGB_VALIDATE_OFFSETS)) return fail(NGB_ERR_INVALID_ARG, "unknown flag");
-  if (dim > 0 && off) return fail(NGB_ERR_INVALID_ARG, "offsets given for a dense batch (dim > 0)");
-  if (dim == 0 && !off) return fail(NGB_ERR_INVALID_ARG, "ragged batch (dim == 0) needs offsets");
-  if (dim == 0 && count > INT32_MAX) return fail(NGB_ERR_UNSUPPORTED, "ragged count >= 2^31");
+  const ngb::ArgCheck a = ngb::check_forward(x, count, dim, off, flags);
+  if (a.status != NGB_OK) return fail(a.status, a.message);
   if (dim == 0) {
     ngb_status st = check_plan(plan, count, (int)sizeof(T));
     if (st != NGB_OK) return st;
   }
   if (count == 0) return NGB_OK;
-  if (!x) return fail(NGB_ERR_INVALID_ARG, "x is NULL");
   if (dim > 0) {
     cudaError_t e = ngb::launch_fixed_forward<T>(x, y, norm, h, code, count, dim,
                                                  !(flags & NGB_VECTOR_SEMANTICS), cs(stream));
     return e == cudaSuccess ? NGB_OK : cuda_fail(e, "forward launch");
   }
   return run_ragged<T>(plan, x, y, norm, h, code, nullptr, nullptr, nullptr, nullptr, off,
-                       (flags & NGB_VALIDATE_OFFSETS) != 0, false, cs(stream));
+                       (flags & NGB_VALIDATE_OFFSETS) != 0, false, a.no_elements, cs(stream));
 }
 
 template <typename T>
 ngb_status backward(const T* y, const T* g, const T* h, const int8_t* code, T* grad, int64_t count, int32_t dim,
                     const int64_t* off, ngb_plan* plan, uint32_t flags, ngb_stream_t stream) {
   g_last_error.clear();
-  if (count < 0) return fail(NGB_ERR_INVALID_ARG, "count < 0");
-  if (dim < 0) return fail(NGB_ERR_INVALID_ARG, "dim < 0");
-  if (dim > NGB_MAX_LEN) return fail(NGB_ERR_UNSUPPORTED, "dim > NGB_MAX_LEN");
-  if (flags & ~(NGB_VECTOR_SEMANTICS | NGB_VALIDATE_OFFSETS)) return fail(NGB_ERR_INVALID_ARG, "unknown flag");
-  if (dim > 0 && off) return fail(NGB_ERR_INVALID_ARG, "offsets given for a dense batch (dim > 0)");
-  if (dim == 0 && !off) return fail(NGB_ERR_INVALID_ARG, "ragged batch (dim == 0) needs offsets");
-  if (dim == 0 && count > INT32_MAX) return fail(NGB_ERR_UNSUPPORTED, "ragged count >= 2^31");
+  const ngb::ArgCheck a = ngb::check_backward(y, g, h, code, grad, count, dim, off, flags);
+  if (a.status != NGB_OK) return fail(a.status, a.message);
   if (dim == 0) {
     ngb_status st = check_plan(plan, count, (int)sizeof(T));
     if (st != NGB_OK) return st;
   }
   if (count == 0) return NGB_OK;
-  if (!y || !g || !h || !code || !grad) return fail(NGB_ERR_INVALID_ARG, "y, g, saved_h, saved_code, grad are required");
   if (dim > 0) {
     cudaError_t e = ngb::launch_fixed_backward<T>(y, g, h, code, grad, count, dim, cs(stream));
     return e == cudaSuccess ? NGB_OK : cuda_fail(e, "backward launch");
   }
   return run_ragged<T>(plan, y, nullptr, nullptr, nullptr, nullptr, g, h, code, grad, off,
-                       (flags & NGB_VALIDATE_OFFSETS) != 0, true, cs(stream));
+                       (flags & NGB_VALIDATE_OFFSETS) != 0, true, a.no_elements, cs(stream));
 }
 
 }  // namespace

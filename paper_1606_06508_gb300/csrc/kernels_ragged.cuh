@@ -46,8 +46,10 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
     if (i < count) {
       const int64_t s = off[i], e = off[i + 1];
       const int64_t n = e - s;
+      // capacity > 0: ends past the caller's buffer are bad; capacity < 0: the
+      // batch has no element array, so every vector of positive length is bad
       const bool bad = n < 0 || n > MAX_LEN || s < 0 || (capacity > 0 && e > capacity) ||
-                       (validate && i == 0 && s != 0);
+                       (capacity < 0 && n > 0) || (validate && i == 0 && s != 0);
       if (bad) {
         atomicOr(sc.status, 1);
       } else if (n == 0) {

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "normgb.h"
+#include "ngb_args.h"
 #include "ngb_internal.h"
 
 namespace {
@@ -45,13 +46,9 @@ extern "C" ngb_status normalize_ragged_f32_noalloc(const float* x, float* y, flo
                                                    int8_t* saved_code, int64_t count, const int64_t* offsets,
                                                    uint32_t flags, ngb_stream_t stream) {
   ngb::set_last_error("");
-  if (count < 0) return ngb::set_last_error("count < 0"), NGB_ERR_INVALID_ARG;
-  if (count > NGB_NOALLOC_MAX_COUNT)
-    return ngb::set_last_error("count exceeds NGB_NOALLOC_MAX_COUNT (262144); use a plan for larger batches"),
-           NGB_ERR_UNSUPPORTED;
-  if (flags & ~(uint32_t)NGB_VALIDATE_OFFSETS) return ngb::set_last_error("unknown flag"), NGB_ERR_INVALID_ARG;
+  const ngb::ArgCheck a = ngb::check_noalloc(x, count, offsets, flags);
+  if (a.status != NGB_OK) return ngb::set_last_error(a.message), a.status;
   if (count == 0) return NGB_OK;
-  if (!x || !offsets) return ngb::set_last_error("x and offsets are required"), NGB_ERR_INVALID_ARG;
   int32_t* base = nullptr;
   cudaError_t e = scratch_for_current_device(&base);
   if (e != cudaSuccess)
@@ -66,7 +63,7 @@ extern "C" ngb_status normalize_ragged_f32_noalloc(const float* x, float* y, flo
   ngb::RaggedMapping map{8, 8192, 256, 0};
   map.grid_blocks = ngb::ragged_full_wave<float>(map, false);
   e = ngb::launch_ragged<float>(x, y, norm, saved_h, saved_code, nullptr, nullptr, nullptr, nullptr, offsets, count,
-                                0, (flags & NGB_VALIDATE_OFFSETS) != 0, map, sc, false,
+                                ngb::classifier_capacity(0, a.no_elements), (flags & NGB_VALIDATE_OFFSETS) != 0, map, sc, false,
                                 reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return ngb::set_last_error(std::string("launch: ") + cudaGetErrorString(e)), NGB_ERR_CUDA;
   return NGB_OK;

@@ -12,6 +12,7 @@ from gpu_util import assert_bits
 from paper_1606_06508_gb300 import synth
 
 NP = {"f32": np.float32, "f64": np.float64}
+RAGGED_COUNTS = (1, 2, 19, 40, 257)  # count 1 is one empty vector: its element buffers are NULL
 TD = {"f32": torch.float32, "f64": torch.float64}
 
 

@@ -46,7 +46,7 @@ def test_dense_guards_and_parity(env, f, shift, dim, counts):
 def test_ragged_guards_and_parity(env, f, shift):
     from paper_1606_06508_gb300 import api
     lib, stream, sync, dev = env
-    for count in (1, 2, 19, 40, 257):
+    for count in gc.RAGGED_COUNTS:
         lengths = gc.ragged_lengths_with_edges(count, seed=count)
         off = synth.offsets_from_lengths(lengths)
         x = synth.ragged_values(lengths, gc.NP[f], seed=count)

@@ -230,3 +230,44 @@ def test_ragged_small_f64_integer_pipe_limits(dev):
         assert_bits(_np(c), oc, tag + " code")
         gr = api.normalize_backward(y, gt, h, c, offt, plan=plan)
         assert_bits(_np(gr), og, tag + " grad")
+
+
+@pytest.mark.parametrize("f", ["f32", "f64"])
+def test_ragged_without_elements(dev, f):
+    """A ragged batch whose element arrays are NULL (every vector empty, as a
+    zero-element torch tensor gives): accepted, norms +0 and code 'zero' for
+    the empty vectors; a vector of positive length in such a batch is skipped
+    and reported as bad offsets, its outputs untouched; the backward call
+    with NULL y, g and grad writes nothing and reports the same."""
+    import torch
+    from paper_1606_06508_gb300 import _lib as L
+    from paper_1606_06508_gb300 import api
+    td = torch.float32 if f == "f32" else torch.float64
+    fwd = L.normalize_f32 if f == "f32" else L.normalize_f64
+    bwd = L.normalize_backward_f32 if f == "f32" else L.normalize_backward_f64
+    stream = torch.cuda.current_stream().cuda_stream
+    for lengths, bad in (([0], False), ([0, 0, 0], False), ([0, 3, 0], True)):
+        count = len(lengths)
+        off = _to(dev, synth.offsets_from_lengths(np.array(lengths, np.int64)))
+        plan = api.Plan(count, td)
+        r = torch.full((count,), float("nan"), dtype=td, device=dev)
+        h = torch.full((count,), float("nan"), dtype=td, device=dev)
+        c = torch.full((count,), 77, dtype=torch.int8, device=dev)
+        for graphs in (True, False):
+            plan.set_graphs(graphs)
+            st = fwd(None, None, r.data_ptr(), h.data_ptr(), c.data_ptr(), count, 0, off.data_ptr(), plan.handle, 0,
+                     stream)
+            assert st == L.NGB_OK, L.last_error()
+            assert plan.query_status() == (L.NGB_ERR_BAD_OFFSETS if bad else L.NGB_OK)
+            empty = np.array(lengths) == 0
+            rn, hn, cn = _np(r), _np(h), _np(c)
+            assert np.all(rn[empty] == 0) and not np.any(np.signbit(rn[empty])) and np.all(hn[empty] == 0)
+            assert np.all(cn[empty] == L.NGB_CODE_ZERO)
+            assert np.all(np.isnan(rn[~empty])) and np.all(cn[~empty] == 77)
+            st = bwd(None, None, h.data_ptr(), c.data_ptr(), None, count, 0, off.data_ptr(), plan.handle, 0, stream)
+            assert st == L.NGB_OK, L.last_error()
+            assert plan.query_status() == (L.NGB_ERR_BAD_OFFSETS if bad else L.NGB_OK)
+        # the torch-facing helper on an empty values tensor
+        y = api.normalize(torch.empty(0, dtype=td, device=dev), off, plan=plan)
+        assert y.numel() == 0
+        plan.close()
