@@ -232,46 +232,134 @@ def cpu_baseline(name: str, seconds: float = 10.0, single_seconds: float = 3.0):
 # ---------------------------------------------------------------------------- parity of the timed outputs
 def _bits_mismatch(a, b):
     ui = np.uint32 if a.dtype == np.float32 else np.uint64
+    a, b = a.reshape(-1), b.reshape(-1)
     nan = np.isnan(a) & np.isnan(b)
     return int(np.count_nonzero((a.view(ui) != b.view(ui)) & ~nan))
 
 
-def parity_dense(x, y, dim, k=1 << 14, grad=None, g=None):
-    import torch
+def parity_full(x, y, dim, off=None, grad=None, g=None):
+    """Every output value of the last timed step against the oracle on the same
+    inputs (the oracle on all host cores over contiguous vector ranges), after
+    the timed region: y, and the gradient of a forward + backward step."""
     import oracle
-    n = x.shape[0]
-    rng = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([np.arange(min(n, 256)), rng.choice(n, min(n, k), replace=False),
-                                    np.arange(max(0, n - 256), n)]))
-    it = torch.from_numpy(idx).to(x.device)
-    xs = x[it].cpu().numpy().reshape(-1)
-    oy, _, oh, oc = oracle.normalize(xs, dim=dim)
-    bad = _bits_mismatch(y[it].cpu().numpy().reshape(-1), oy)
+    threads = cpu_threads()
+    t0 = time.perf_counter()
+    xh = x.cpu().numpy().reshape(-1)
+    offh = off.cpu().numpy() if off is not None else None
+    oy, _, oh, oc = oracle.normalize_threads(xh, dim, offh, threads=threads)
+    del xh
+    bad = _bits_mismatch(y.cpu().numpy(), oy)
+    values = int(y.numel())
     if grad is not None:
-        og = oracle.backward(oy, g[it].cpu().numpy().reshape(-1), oh, oc, dim=dim)
-        bad += _bits_mismatch(grad[it].cpu().numpy().reshape(-1), og)
-    return {"sampled_vectors": int(idx.size), "mismatching_values": bad, "max_ulp_vs_oracle": 0 if bad == 0 else None}
+        og = oracle.backward_threads(oy, g.cpu().numpy().reshape(-1), oh, oc, dim=dim, offsets=offh,
+                                     threads=threads)
+        bad += _bits_mismatch(grad.cpu().numpy(), og)
+        values += int(grad.numel())
+    count = oh.size
+    return {"vectors": int(count), "values_compared": values, "mismatching_values": bad,
+            "max_ulp_vs_oracle": 0 if bad == 0 else None,
+            "compared": "every output value of the last timed step (y" + (", grad" if grad is not None else "") +
+                        "), bit for bit",
+            "oracle_threads": threads, "seconds": time.perf_counter() - t0}
 
 
-def parity_ragged(x, off_t, y, k=2048, grad=None, g=None):
+# ---------------------------------------------------------------------------- error vs the exact result
+FMT_NAMES = {"f32": "binary32, u = 2^-24", "f64": "binary64, u = 2^-53"}
+
+
+def _exact_errors(vectors, fmt):
+    """Errors (oracle/exact.py, exact rationals and a 256-bit square root) of
+    computed (x^, r^) pairs, with the paper's bounds per length: ||x^ - x/r||
+    against (3.001 + n/2) u (Lemmas 1, 2, 4; the rounding count of the order
+    CR(n) in place of n for n >= 5), |r^ - r| against (1 + n/2) r u, |sin phi|
+    against 1.001 u (Lemma 1, n = 2, 3), and the largest per-component error
+    in ulps (no bound in the paper; information).  Zero and non-finite inputs
+    are skipped."""
+    from oracle import exact
+    out = {"direction": {"max_u": 0.0, "max_over_bound": 0.0, "n_at_max": None},
+           "norm": {"max_u": 0.0, "max_over_bound": 0.0, "n_at_max": None},
+           "sin_phi": {"max_u": 0.0, "bound_u": float(exact.SIN_BOUND_U), "applies_to": "n = 2, 3 (Lemma 1)"},
+           "component_ulp_max": 0.0, "vectors_checked": 0, "all_within_bounds": True, "failing_vectors": 0}
+    for x, y, r in vectors:
+        if not np.all(np.isfinite(x)) or not np.any(x != 0):
+            continue
+        n = x.size
+        e = exact.errors(x, y, r, fmt)
+        ok = exact.check(x, y, r, fmt, quaternion=(n == 4)).ok
+        out["vectors_checked"] += 1
+        if not ok:
+            out["all_within_bounds"] = False
+            out["failing_vectors"] += 1
+        db = float(exact.direction_bound(n, fmt.u))
+        d = out["direction"]
+        if e["direction_u"] / db > d["max_over_bound"]:
+            d["max_over_bound"], d["n_at_max"], d["bound_u_at_max"] = e["direction_u"] / db, n, db
+        d["max_u"] = max(d["max_u"], e["direction_u"])
+        if e["norm_u"] is not None:
+            nb = float(exact.norm_bound(n, fmt.u))
+            m = out["norm"]
+            if e["norm_u"] / nb > m["max_over_bound"]:
+                m["max_over_bound"], m["n_at_max"], m["bound_u_at_max"] = e["norm_u"] / nb, n, nb
+            m["max_u"] = max(m["max_u"], e["norm_u"])
+        if n in (2, 3):
+            out["sin_phi"]["max_u"] = max(out["sin_phi"]["max_u"], e["sin_u"])
+        out["component_ulp_max"] = max(out["component_ulp_max"], e["ulp"])
+    return out
+
+
+def accuracy_report(x, y, dim, off=None, k=2000, k_long=200, seed=7, edges=True):
+    """Error against the exact result on a seeded sample of the timed output:
+    k vectors of n <= 4, k_long longer ones.  The norms come from one more
+    library call on the sampled vectors (the timed step writes no norms); its
+    y must equal the timed y bit for bit.  With `edges`, the 64 binary64 edge
+    vectors of the 3-vector workload are normalized by the library and checked
+    the same way."""
     import torch
-    import oracle
-    from paper_1606_06508_gb300 import synth
-    off = off_t.cpu().numpy()
-    n = off.size - 1
-    rng = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([np.arange(min(n, 64)), rng.choice(n, min(n, k), replace=False),
-                                    np.arange(max(0, n - 64), n)]))
-    starts, ends = off[idx], off[idx + 1]
-    sub = synth.offsets_from_lengths(ends - starts)
-    gather = np.concatenate([np.arange(a, b) for a, b in zip(starts, ends)]).astype(np.int64)
-    gt = torch.from_numpy(gather).to(x.device)
-    oy, _, oh, oc = oracle.normalize(x[gt].cpu().numpy(), dim=0, offsets=sub)
-    bad = _bits_mismatch(y[gt].cpu().numpy(), oy)
-    if grad is not None:
-        og = oracle.backward(oy, g[gt].cpu().numpy(), oh, oc, dim=0, offsets=sub)
-        bad += _bits_mismatch(grad[gt].cpu().numpy(), og)
-    return {"sampled_vectors": int(idx.size), "mismatching_values": bad, "max_ulp_vs_oracle": 0 if bad == 0 else None}
+    from oracle import exact
+    from paper_1606_06508_gb300 import api, synth
+    t0 = time.perf_counter()
+    rng = np.random.default_rng(seed)
+    fmt = exact.F32 if x.dtype == torch.float32 else exact.F64
+    if off is None:
+        count = x.numel() // dim
+        kk = min(count, k if dim <= 4 else k_long)
+        idx = np.sort(rng.choice(count, kk, replace=False))
+        it = torch.from_numpy(idx).to(x.device)
+        xs = x.reshape(count, dim)[it].contiguous()
+        ys = y.reshape(count, dim)[it]
+        ys2, rs = api.normalize(xs, return_norm=True)
+        lens = np.full(kk, dim)
+        sub = synth.offsets_from_lengths(lens)
+    else:
+        offh = off.cpu().numpy()
+        count = offh.size - 1
+        n = np.diff(offh)
+        short, long_ = np.flatnonzero(n <= 4), np.flatnonzero(n > 4)
+        idx = np.sort(np.concatenate([rng.choice(short, min(k, short.size), replace=False),
+                                      rng.choice(long_, min(k_long, long_.size), replace=False)]))
+        lens = n[idx]
+        sub = synth.offsets_from_lengths(lens)
+        gather = np.concatenate([np.arange(offh[i], offh[i + 1]) for i in idx]).astype(np.int64)
+        gt = torch.from_numpy(gather).to(x.device)
+        xs, ys = x[gt].contiguous(), y[gt]
+        ys2, rs = api.normalize(xs, torch.from_numpy(sub).to(x.device), return_norm=True)
+    torch.cuda.synchronize()
+    consistent = _bits_mismatch(ys2.cpu().numpy(), ys.cpu().numpy()) == 0
+    xh, yh, rh = xs.cpu().numpy().reshape(-1), ys.cpu().numpy().reshape(-1), rs.cpu().numpy()
+    vecs = [(xh[sub[i]:sub[i + 1]], yh[sub[i]:sub[i + 1]], rh[i]) for i in range(lens.size)]
+    rep = {"format": FMT_NAMES["f32" if fmt is exact.F32 else "f64"],
+           "sample": f"{lens.size} vectors of the timed output (seed {seed}; n <= 4: up to {k}, longer: up to "
+                     f"{k_long})",
+           "norms_from_a_second_call_consistent": bool(consistent),
+           **_exact_errors(vecs, fmt)}
+    if edges:
+        e = synth.edge_vectors_d3_f64()
+        ye, re_ = api.normalize(torch.from_numpy(e).to(x.device), return_norm=True)
+        torch.cuda.synchronize()
+        ye, re_ = ye.cpu().numpy(), re_.cpu().numpy()
+        rep["edge_vectors_d3_f64"] = _exact_errors([(e[i], ye[i], re_[i]) for i in range(e.shape[0])], exact.F64)
+    rep["seconds"] = time.perf_counter() - t0
+    return rep
 
 
 # ---------------------------------------------------------------------------- workloads
@@ -336,7 +424,7 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                           "wide-exponent/N(0,1) components") if count == QUAT_COUNT
                     else f"{count} binary32 quaternions, forward (profiling size)",
                     units=count, bytes=32 * count, dtype="f32", kernel="k_small_vec16<float,4>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 4),
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="16 B read + 16 B written per quaternion")
 
     if name == "fwdbwd_quat":
@@ -355,7 +443,7 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         return Work(desc=f"{n} binary32 quaternions, forward (saving h and code) + backward",
                     units=n, bytes=90 * n, dtype="f32", kernel="k_small_vec16<float,4> + k_small_bwd<float,4>",
                     launches=2, step=step, h2d=[x, g], d2h=[gr],
-                    parity=lambda: parity_dense(x, y, 4, grad=gr, g=g),
+                    parity=lambda: parity_full(x, y, 4, grad=gr, g=g), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="fwd 16+16+4+1, bwd 16+16+4+1+16 per quaternion")
 
     if name in ("rows_f32", "rows_f64"):
@@ -370,7 +458,7 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         return Work(desc=f"{rows} rows of 256 {name[-3:]}, forward, N(0,1) x 2^s per row",
                     units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
                     kernel=('k_rows_half<4>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 256, k=2048),
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 256), accuracy=lambda: accuracy_report(x, y, 256),
                     bytes_model="2 x 256 x s per row",
                     dp_ops=(3 * rows * 256 + 3 * rows) if dt == torch.float64 else None)
 
@@ -399,7 +487,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                              f"int64 offsets, forward, one persistent launch after the classifier",
                         units=cnt, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1), dtype=name[-3:],
                         kernel="k_classify + k_ragged (persistent)", launches=2, step=step, h2d=[x, off], d2h=[y],
-                        parity=lambda: parity_ragged(x, off, y), mapping=list(mapping), plan=plan,
+                        parity=lambda: parity_full(x, y, 0, off=off), accuracy=lambda: accuracy_report(x, y, 0, off=off),
+                        mapping=list(mapping), plan=plan,
                         bytes_model="2 n s per vector + 8 B offsets",
                         dp_ops=(3 * x.numel() + 3 * cnt) if dt == torch.float64 else None)
         g = synth.normal_like_torch(x.shape, dt, seed=41 + seed, device=dev)
@@ -415,7 +504,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         return Work(desc=f"{cnt} ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
                     units=cnt, bytes=5 * x.numel() * s_bytes + 2 * 9 * cnt + 2 * 8 * (cnt + 1), dtype="f64",
                     kernel="k_classify + k_ragged; k_classify + k_ragged_bwd_{blocks,warps,threads}", launches=6,
-                    step=step, h2d=[x, g, off], d2h=[gr], parity=lambda: parity_ragged(x, off, y, grad=gr, g=g),
+                    step=step, h2d=[x, g, off], d2h=[gr], parity=lambda: parity_full(x, y, 0, off=off, grad=gr, g=g),
+                    accuracy=lambda: accuracy_report(x, y, 0, off=off),
                     mapping=list(mapping), plan=plan,
                     bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector",
                     dp_ops=8 * x.numel() + 3 * cnt)
@@ -430,7 +520,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                                     s.cuda_stream), "quat_f64")
         return Work(desc=f"{n} binary64 quaternions (components sign x U[1,2) x 2^e, e in [-30,30]), forward",
                     units=n, bytes=64 * n, dtype="f64", kernel="k_small_direct<double,4>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 4),
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 4),
+                    accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="32 B read + 32 B written per quaternion", dp_ops=15 * n)
 
     if name == "vec3_f64":
@@ -444,7 +535,7 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                                     s.cuda_stream), "vec3")
         return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
                     units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_direct<double,3>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_dense(x, y, 3, k=cnt), flush=True,
+                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 3), accuracy=lambda: accuracy_report(x, y, 3, k=4000), flush=True,
                     bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
     raise ValueError(f"unknown workload {name}")
 
@@ -715,6 +806,7 @@ def run_ours(args):
                          "steps": e2e_steps,
                          "note": "pinned host inputs -> device, library call(s), device result -> pinned host"}
         result["parity"] = w.parity()
+        result["accuracy"] = w.accuracy()
         if world == 1:
             if not args.no_extras and args.workload == "quat":
                 del hin, hout

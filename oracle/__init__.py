@@ -188,6 +188,45 @@ def normalize_threads(x, dim: int, offsets=None, flags: int = 0, threads: int = 
     return y, norm, h, code
 
 
+def backward_threads(y, g, saved_h, saved_code, dim: int = 0, offsets=None, threads: int = 1):
+    """:func:`backward` run over contiguous vector ranges on ``threads`` host
+    threads (ctypes releases the GIL during each call).  Same results."""
+    y = np.ascontiguousarray(y)
+    g = np.ascontiguousarray(g, dtype=y.dtype)
+    saved_h = np.ascontiguousarray(saved_h, dtype=y.dtype)
+    saved_code = np.ascontiguousarray(saved_code, dtype=np.int8)
+    off = None if dim > 0 else np.ascontiguousarray(offsets, dtype=np.int64)
+    n_vec = saved_h.size
+    grad = np.empty_like(y)
+    fn = getattr(_load(), f"oracle_backward_{_sfx(y.dtype)}")
+    bounds = np.linspace(0, n_vec, threads + 1).astype(np.int64)
+    isz = y.itemsize
+    errors = []
+
+    def work(a, b):
+        if b <= a:
+            return
+        if dim > 0:
+            shift = int(a) * dim * isz
+            offp = None
+        else:  # absolute offsets: keep the base pointers, move the offsets
+            shift = 0
+            offp = off.ctypes.data + int(a) * 8
+        rc = fn(y.ctypes.data + shift, g.ctypes.data + shift, saved_h.ctypes.data + int(a) * isz,
+                saved_code.ctypes.data + int(a), int(b - a), dim, offp, grad.ctypes.data + shift)
+        if rc:
+            errors.append(rc)
+
+    ts = [threading.Thread(target=work, args=(bounds[i], bounds[i + 1])) for i in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errors:
+        raise ValueError(f"oracle failed: {errors}")
+    return grad
+
+
 def rotation(q):
     """Section 4: rotation matrices [count, 3, 3] of quaternions [count, 4]
     (scalar part last) normalized by Algorithm 7, and their norms."""

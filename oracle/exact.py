@@ -6,7 +6,11 @@ Every input is a binary32 or binary64 number, hence an exact dyadic rational.
 The true norm r = sqrt(x_1^2 + ... + x_n^2) is irrational in general, so each
 bound of the form |a - b/r| <= e is decided by squaring both sides with
 their signs tracked, in exact rational arithmetic (``fractions``).  Nothing
-here uses floating-point rounding, the oracle, or the CUDA library.
+here uses floating-point rounding, the oracle's C code, or the CUDA library.
+
+TEST INFRASTRUCTURE: it pins the oracle (tests/) and measures the error of
+computed results against the exact ones (the benchmark's accuracy report,
+after its timed region); the library never imports it.
 """
 from __future__ import annotations
 
@@ -229,3 +233,48 @@ def round_nearest_even(q: Fr, fmt: Fmt) -> float:
     if v > fmt.omega:
         return sign * math.inf
     return sign * float(v)
+
+
+def _ulp(v: Fr, fmt: Fmt) -> Fr:
+    """Spacing of the binary32/binary64 numbers in the binade of |v| (alpha for
+    v = 0 and for subnormal magnitudes)."""
+    p = 24 if fmt is F32 else 53
+    a = abs(v)
+    if a == 0:
+        return fmt.alpha
+    e = a.numerator.bit_length() - a.denominator.bit_length()
+    if Fr(2) ** e > a:
+        e -= 1
+    q = Fr(2) ** (e - (p - 1))
+    return q if q > fmt.alpha else fmt.alpha
+
+
+def errors(x, yhat, rhat, fmt: Fmt) -> dict:
+    """Measured errors of one computed (x^, r^) for a finite nonzero x, in
+    units of u, with the exact norm carried to 256 bits (reporting, not a
+    decision; check() decides the bounds exactly):
+      direction_u  ||x^ - x/r||_2 / u         (Lemmas 1, 2, 4)
+      norm_u       |r^ - r| / (r u)           (Lemmas 1, 2, 4), None if r^ is
+                   not finite
+      sin_u        |sin phi| / u, phi the angle between x^ and x (Lemma 1)
+      ulp          max_k |x^_k - x_k/r| / ulp(x_k/r)  (per component)."""
+    xs = [fr(v) for v in x]
+    if not all(math.isfinite(float(v)) for v in yhat):
+        return {"direction_u": math.inf, "norm_u": math.inf, "sin_u": math.inf, "ulp": math.inf}
+    ys = [fr(v) for v in yhat]
+    s = sum(v * v for v in xs)
+    r = _sqrt_approx(s)
+    u = fmt.u
+    A = sum(v * v for v in ys)
+    P = sum(a * b for a, b in zip(ys, xs))
+    e2 = A - 2 * P / r + 1
+    direction = math.sqrt(max(float(e2), 0.0)) / float(u)
+    sin2 = (s * A - P * P) / (s * A) if A > 0 else Fr(1)
+    sin_u = math.sqrt(max(float(sin2), 0.0)) / float(u)
+    rh = float(rhat)
+    norm_u = float(abs(fr(rh) - r) / r / u) if math.isfinite(rh) else None
+    ulp = 0.0
+    for xk, yk in zip(xs, ys):
+        ex = xk / r
+        ulp = max(ulp, float(abs(yk - ex) / _ulp(ex, fmt)))
+    return {"direction_u": direction, "norm_u": norm_u, "sin_u": sin_u, "ulp": ulp}

@@ -61,3 +61,32 @@ def test_cpu_baseline_reports_all_cores_and_one_thread(name):
     assert cb["cores"] == bench.cpu_threads()
     st = cb["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0 and st["GB_per_s"] > 0
+
+
+def test_exact_error_report_on_oracle_outputs():
+    """The bench's error report (oracle/exact.py) on the oracle's own results:
+    every vector within the paper's bounds, the 64 binary64 edge vectors
+    included; a result pushed 4 ulps off in one component is reported as
+    outside the bound with its ulp error."""
+    import numpy as np
+    import oracle
+    from oracle import exact
+    from paper_1606_06508_gb300 import synth
+    q = synth.quaternions_f32(300, seed=1)
+    y, r, _, _ = oracle.normalize(q.reshape(-1), dim=4)
+    y = y.reshape(-1, 4)
+    rep = bench._exact_errors([(q[i], y[i], r[i]) for i in range(q.shape[0])], exact.F32)
+    assert rep["all_within_bounds"] and rep["vectors_checked"] == 300
+    assert 0 < rep["direction"]["max_u"] <= 5.001 and rep["direction"]["n_at_max"] == 4
+    assert 0 <= rep["norm"]["max_u"] <= 3 and rep["component_ulp_max"] > 0
+    e = synth.edge_vectors_d3_f64()
+    ye, re_, _, _ = oracle.normalize(e.reshape(-1), dim=3)
+    ye = ye.reshape(-1, 3)
+    rep = bench._exact_errors([(e[i], ye[i], re_[i]) for i in range(64)], exact.F64)
+    assert rep["all_within_bounds"] and rep["vectors_checked"] == 64 - 4  # the four zero vectors are skipped
+    assert rep["sin_phi"]["max_u"] <= 1.001
+    bad = y[0].copy()
+    k = int(np.argmax(np.abs(bad)))
+    bad[k] = np.float32(bad[k] + np.float32(4) * np.spacing(bad[k]))
+    rep = bench._exact_errors([(q[0], bad, r[0])], exact.F32)
+    assert not rep["all_within_bounds"] and rep["component_ulp_max"] >= 3.5

@@ -5,7 +5,7 @@ import math
 import os
 from fractions import Fraction as Fr
 
-import exact
+from oracle import exact
 import test_oracle_pins as pins
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")

@@ -19,9 +19,9 @@ import os
 import numpy as np
 import pytest
 
-import exact
+from oracle import exact
 from gpu_util import full_grid_two_f32
-from exact import F32, F64, fr
+from oracle.exact import F32, F64, fr
 from paper_1606_06508_gb300 import synth
 
 DT = {"f32": np.float32, "f64": np.float64}

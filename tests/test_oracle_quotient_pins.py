@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import oracle
-from exact import F32, F64, check
+from oracle.exact import F32, F64, check
 
 FMT = {np.float32: F32, np.float64: F64}
 
