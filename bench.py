@@ -271,7 +271,8 @@ def _exact_errors(vectors, fmt):
     """Errors (oracle/exact.py, exact rationals and a 256-bit square root) of
     computed (x^, r^) pairs, with the paper's bounds per length: ||x^ - x/r||
     against (3.001 + n/2) u (Lemmas 1, 2, 4; the rounding count of the order
-    CR(n) in place of n for n >= 5), |r^ - r| against (1 + n/2) r u, |sin phi|
+    CR(n) in place of n for n >= 5), |r^ - r| beyond the alpha/2 the lemmas
+    allow for a subnormal norm, against (1 + n/2) r u, |sin phi|
     against 1.001 u (Lemma 1, n = 2, 3), and the largest per-component error
     in ulps (no bound in the paper; information).  Zero and non-finite inputs
     are skipped."""
@@ -372,6 +373,8 @@ class Work:
         self.flush = False
         self.dp_ops = None
         self.__dict__.update(kw)
+        ptrs = {k: t.data_ptr() for k, t in self.arrays.items()}
+        self.step = lambda: self.launch(ptrs)
 
 
 DP_OPS_MODEL = ("binary64 operations of the paper's sequence done on the FP64 pipe: 3 per element (square, "
@@ -407,6 +410,11 @@ def dp_roofline(w, ms_per_step, rate):
 
 
 def build_work(name, count, rank, torch, L, api, synth, mapping=None):
+    """The workload `name`: its arrays (device tensors), `launch(p)` running
+    one step of library calls on the pointers p[name] (so that the same step
+    runs on device buffers or, for the end-to-end figure, on pinned host
+    buffers), which arrays are the step's inputs and results, its units and
+    algorithmic bytes, and the post-timing checks."""
     dev = torch.device("cuda", torch.cuda.current_device())
     s = torch.cuda.current_stream()
     seed = 1000 * rank
@@ -414,17 +422,17 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
     if name == "quat":
         x = synth.quaternions_f32_torch(count, seed=1 + seed, device=dev)
         y = torch.empty_like(x)
-        xp, yp = x.data_ptr(), y.data_ptr()
 
-        def step():
-            st = L.normalize_f32(xp, yp, None, None, None, count, 4, None, None, 0, s.cuda_stream)
+        def launch(p):
+            st = L.normalize_f32(p["x"], p["y"], None, None, None, count, 4, None, None, 0, s.cuda_stream)
             if st:
                 L.check(st, "normalize_f32")
         return Work(desc=("2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 "
                           "wide-exponent/N(0,1) components") if count == QUAT_COUNT
                     else f"{count} binary32 quaternions, forward (profiling size)",
                     units=count, bytes=32 * count, dtype="f32", kernel="k_small_vec16<float,4>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
+                    arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
+                    parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="16 B read + 16 B written per quaternion")
 
     if name == "fwdbwd_quat":
@@ -435,14 +443,14 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         h = torch.empty(n, device=dev)
         c = torch.empty(n, dtype=torch.int8, device=dev)
 
-        def step():
-            L.check(L.normalize_f32(x.data_ptr(), y.data_ptr(), None, h.data_ptr(), c.data_ptr(), n, 4, None, None, 0,
-                                    s.cuda_stream), "fwd")
-            L.check(L.normalize_backward_f32(y.data_ptr(), g.data_ptr(), h.data_ptr(), c.data_ptr(), gr.data_ptr(),
-                                             n, 4, None, None, 0, s.cuda_stream), "bwd")
+        def launch(p):
+            L.check(L.normalize_f32(p["x"], p["y"], None, p["h"], p["c"], n, 4, None, None, 0, s.cuda_stream), "fwd")
+            L.check(L.normalize_backward_f32(p["y"], p["g"], p["h"], p["c"], p["gr"], n, 4, None, None, 0,
+                                             s.cuda_stream), "bwd")
         return Work(desc=f"{n} binary32 quaternions, forward (saving h and code) + backward",
                     units=n, bytes=90 * n, dtype="f32", kernel="k_small_vec16<float,4> + k_small_bwd<float,4>",
-                    launches=2, step=step, h2d=[x, g], d2h=[gr],
+                    launches=2, arrays={"x": x, "g": g, "y": y, "h": h, "c": c, "gr": gr}, inputs=["x", "g"],
+                    results=["gr"], launch=launch,
                     parity=lambda: parity_full(x, y, 4, grad=gr, g=g), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="fwd 16+16+4+1, bwd 16+16+4+1+16 per quaternion")
 
@@ -453,12 +461,13 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         y = torch.empty_like(x)
         fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
 
-        def step():
-            L.check(fn(x.data_ptr(), y.data_ptr(), None, None, None, rows, 256, None, None, 0, s.cuda_stream), "rows")
+        def launch(p):
+            L.check(fn(p["x"], p["y"], None, None, None, rows, 256, None, None, 0, s.cuda_stream), "rows")
         return Work(desc=f"{rows} rows of 256 {name[-3:]}, forward, N(0,1) x 2^s per row",
                     units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
                     kernel=('k_rows_half<4>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 256), accuracy=lambda: accuracy_report(x, y, 256),
+                    arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
+                    parity=lambda: parity_full(x, y, 256), accuracy=lambda: accuracy_report(x, y, 256),
                     bytes_model="2 x 256 x s per row",
                     dp_ops=(3 * rows * 256 + 3 * rows) if dt == torch.float64 else None)
 
@@ -480,13 +489,14 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
         s_bytes = x.element_size()
         if not fb:
-            def step():
-                L.check(fn(x.data_ptr(), y.data_ptr(), None, None, None, cnt, 0, off.data_ptr(), plan.handle, 0,
-                           s.cuda_stream), "ragged")
+            def launch(p):
+                L.check(fn(p["x"], p["y"], None, None, None, cnt, 0, p["off"], plan.handle, 0, s.cuda_stream),
+                        "ragged")
             return Work(desc=f"{cnt} ragged {name[-3:]} vectors (40% of length 2-4, else log-uniform [5,4096]), "
                              f"int64 offsets, forward, one persistent launch after the classifier",
                         units=cnt, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1), dtype=name[-3:],
-                        kernel="k_classify + k_ragged (persistent)", launches=2, step=step, h2d=[x, off], d2h=[y],
+                        kernel="k_classify + k_ragged (persistent)", launches=2,
+                        arrays={"x": x, "off": off, "y": y}, inputs=["x", "off"], results=["y"], launch=launch,
                         parity=lambda: parity_full(x, y, 0, off=off), accuracy=lambda: accuracy_report(x, y, 0, off=off),
                         mapping=list(mapping), plan=plan,
                         bytes_model="2 n s per vector + 8 B offsets",
@@ -496,15 +506,16 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         h = torch.empty(cnt, dtype=dt, device=dev)
         c = torch.empty(cnt, dtype=torch.int8, device=dev)
 
-        def step():
-            L.check(fn(x.data_ptr(), y.data_ptr(), None, h.data_ptr(), c.data_ptr(), cnt, 0, off.data_ptr(),
-                       plan.handle, 0, s.cuda_stream), "fwd")
-            L.check(L.normalize_backward_f64(y.data_ptr(), g.data_ptr(), h.data_ptr(), c.data_ptr(), gr.data_ptr(),
-                                             cnt, 0, off.data_ptr(), plan.handle, 0, s.cuda_stream), "bwd")
+        def launch(p):
+            L.check(fn(p["x"], p["y"], None, p["h"], p["c"], cnt, 0, p["off"], plan.handle, 0, s.cuda_stream), "fwd")
+            L.check(L.normalize_backward_f64(p["y"], p["g"], p["h"], p["c"], p["gr"], cnt, 0, p["off"], plan.handle, 0,
+                                             s.cuda_stream), "bwd")
         return Work(desc=f"{cnt} ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
                     units=cnt, bytes=5 * x.numel() * s_bytes + 2 * 9 * cnt + 2 * 8 * (cnt + 1), dtype="f64",
                     kernel="k_classify + k_ragged; k_classify + k_ragged_bwd_{blocks,warps,threads}", launches=6,
-                    step=step, h2d=[x, g, off], d2h=[gr], parity=lambda: parity_full(x, y, 0, off=off, grad=gr, g=g),
+                    arrays={"x": x, "g": g, "off": off, "y": y, "h": h, "c": c, "gr": gr},
+                    inputs=["x", "g", "off"], results=["gr"], launch=launch,
+                    parity=lambda: parity_full(x, y, 0, off=off, grad=gr, g=g),
                     accuracy=lambda: accuracy_report(x, y, 0, off=off),
                     mapping=list(mapping), plan=plan,
                     bytes_model="fwd 2ns + 9 + 8, bwd 3ns + 9 + 8 per vector",
@@ -515,13 +526,12 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         x = synth.quaternions_f64_torch(n, seed=5 + seed, device=dev)
         y = torch.empty_like(x)
 
-        def step():
-            L.check(L.normalize_f64(x.data_ptr(), y.data_ptr(), None, None, None, n, 4, None, None, 0,
-                                    s.cuda_stream), "quat_f64")
+        def launch(p):
+            L.check(L.normalize_f64(p["x"], p["y"], None, None, None, n, 4, None, None, 0, s.cuda_stream), "quat_f64")
         return Work(desc=f"{n} binary64 quaternions (components sign x U[1,2) x 2^e, e in [-30,30]), forward",
                     units=n, bytes=64 * n, dtype="f64", kernel="k_small_direct<double,4>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 4),
-                    accuracy=lambda: accuracy_report(x, y, 4),
+                    arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
+                    parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="32 B read + 32 B written per quaternion", dp_ops=15 * n)
 
     if name == "vec3_f64":
@@ -530,13 +540,13 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
         y = torch.empty_like(x)
         cnt = x.shape[0]
 
-        def step():
-            L.check(L.normalize_f64(x.data_ptr(), y.data_ptr(), None, None, None, cnt, 3, None, None, 0,
-                                    s.cuda_stream), "vec3")
+        def launch(p):
+            L.check(L.normalize_f64(p["x"], p["y"], None, None, None, cnt, 3, None, None, 0, s.cuda_stream), "vec3")
         return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
                     units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_direct<double,3>", launches=1,
-                    step=step, h2d=[x], d2h=[y], parity=lambda: parity_full(x, y, 3), accuracy=lambda: accuracy_report(x, y, 3, k=4000), flush=True,
-                    bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
+                    arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
+                    parity=lambda: parity_full(x, y, 3), accuracy=lambda: accuracy_report(x, y, 3, k=4000),
+                    flush=True, bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
     raise ValueError(f"unknown workload {name}")
 
 
@@ -772,44 +782,82 @@ def run_ours(args):
         dp = dp_roofline(w, ms / args.steps, rate)
         if dp:
             result["dp_roofline"] = dp
-    # e2e through pinned host buffers: H2D of the step's inputs, the call, D2H of its result
+    if args.kernels_only:
+        if rank == 0:
+            result["kernels_only"] = True
+            print(json.dumps(result), flush=True)
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+    # e2e through the library's public calls with the step's inputs and results
+    # in pinned host memory.  Main figure: the calls are given the host
+    # pointers, and the kernels read the inputs and write the results over the
+    # host link (NVLink-C2C) themselves -- the host-to-device and device-to-host
+    # transfers happen inside every timed step, with no staging copy.  Beside
+    # it: the same step staged by copy engines (inputs copied to the device,
+    # the device call, results copied back).
     e2e_steps = max(1, min(args.steps, 20))
-    hin = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True).copy_(t) for t in w.h2d]
-    hout = [torch.empty(t.shape, dtype=t.dtype, pin_memory=True) for t in w.d2h]
+    host = {k: torch.empty(w.arrays[k].shape, dtype=w.arrays[k].dtype, pin_memory=True)
+            for k in w.inputs + w.results}
+    for k in w.inputs:
+        host[k].copy_(w.arrays[k])
+    zptrs = {k: t.data_ptr() for k, t in w.arrays.items()}
+    zptrs.update({k: t.data_ptr() for k, t in host.items()})
     torch.cuda.synchronize()
 
-    def e2e_step():
-        for hd, dd in zip(hin, w.h2d):
-            dd.copy_(hd, non_blocking=True)
+    def zero_copy_step():
+        w.launch(zptrs)
+
+    def staged_step():
+        for k in w.inputs:
+            w.arrays[k].copy_(host[k], non_blocking=True)
         w.step()
-        for hd, dd in zip(hout, w.d2h):
-            hd.copy_(dd, non_blocking=True)
-    e2e_step()
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(s)
-    for _ in range(e2e_steps):
-        e2e_step()
-    b.record(s)
-    torch.cuda.synchronize()
-    ems = a.elapsed_time(b)
-    if world > 1:
-        t = torch.tensor([ems], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ems = float(t.item())
+        for k in w.results:
+            host[k].copy_(w.arrays[k], non_blocking=True)
+
+    def time_e2e(fn):
+        fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s)
+        for _ in range(e2e_steps):
+            fn()
+        b.record(s)
+        torch.cuda.synchronize()
+        t_ms = a.elapsed_time(b)
+        if world > 1:
+            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return t_ms
+
+    zms = time_e2e(zero_copy_step)
+    zero_copy_results = {k: host[k].clone() for k in w.results}
+    sms = time_e2e(staged_step)  # leaves the device step's results in host[k]
+    same = all(_bits_mismatch(zero_copy_results[k].numpy(), host[k].numpy()) == 0 for k in w.results)
     if rank == 0:
-        result["e2e"] = {"value": world * e2e_steps * w.units / (ems * 1e-3), "unit": "vectors/s",
-                         "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in w.h2d),
-                         "d2h_bytes_per_step": sum(t.numel() * t.element_size() for t in w.d2h),
-                         "steps": e2e_steps,
-                         "note": "pinned host inputs -> device, library call(s), device result -> pinned host"}
+        h2d = sum(host[k].numel() * host[k].element_size() for k in w.inputs)
+        d2h = sum(host[k].numel() * host[k].element_size() for k in w.results)
+        result["e2e"] = {"value": world * e2e_steps * w.units / (zms * 1e-3), "unit": "vectors/s",
+                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                         "ms_per_step": zms / e2e_steps,
+                         "link_GB_per_s": (h2d + d2h) * e2e_steps / (zms * 1e-3) / 1e9,
+                         "note": "inputs and results in pinned host memory; the library calls get the host pointers "
+                                 "and their kernels read the inputs and write the results over the host link "
+                                 "(zero-copy), inside every timed step",
+                         "results_equal_device_path": bool(same),
+                         "staged": {"value": world * e2e_steps * w.units / (sms * 1e-3), "unit": "vectors/s",
+                                    "ms_per_step": sms / e2e_steps,
+                                    "note": "copy engines: pinned host inputs -> device, the device call(s), device "
+                                            "results -> pinned host, one after the other"}}
         result["parity"] = w.parity()
         result["accuracy"] = w.accuracy()
         if world == 1:
             if not args.no_extras and args.workload == "quat":
-                del hin, hout
+                del host, zero_copy_results
                 w = None
                 torch.cuda.empty_cache()
                 result["also"] = extras(torch, L, api, synth, peak, rate)
@@ -829,6 +877,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=WORKLOAD_NAMES, default="quat")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="profiling: time the steps and print the line without the end-to-end figure, the checks "
+                         "and the CPU baseline")
     ap.add_argument("--mapping", type=lambda v: [int(t) for t in v.split(",")], default=None,
                     help="ragged workloads: thread_max,warp_max,block_threads,grid_blocks instead of autotuning "
                          "(profiling)")

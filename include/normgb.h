@@ -20,9 +20,13 @@
  * steps.
  *
  * Conventions for every entry point:
- *   - Array arguments are DEVICE pointers owned by the caller.  Vectors are
- *     stored contiguously: a dense batch is [count][dim] row-major (AoS); a
- *     ragged batch packs vector i at x[offsets[i] .. offsets[i+1]).
+ *   - Array arguments are addresses the GPU can access, owned by the caller:
+ *     device memory, or pinned host memory (cudaHostAlloc, cudaMallocHost,
+ *     cudaHostRegister), which the kernels then read and write directly over
+ *     the host link (zero-copy: no staging copy; on Grace-Blackwell the
+ *     NVLink-C2C link).  Vectors are stored contiguously: a dense batch is
+ *     [count][dim] row-major (AoS); a ragged batch packs vector i at
+ *     x[offsets[i] .. offsets[i+1]).
  *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *     default stream).  Argument errors are detected on the host before any
  *     work is queued.  Data-dependent errors (bad ragged offsets) never stop a

@@ -254,8 +254,9 @@ def errors(x, yhat, rhat, fmt: Fmt) -> dict:
     units of u, with the exact norm carried to 256 bits (reporting, not a
     decision; check() decides the bounds exactly):
       direction_u  ||x^ - x/r||_2 / u         (Lemmas 1, 2, 4)
-      norm_u       |r^ - r| / (r u)           (Lemmas 1, 2, 4), None if r^ is
-                   not finite
+      norm_u       max(|r^ - r| - e, 0) / (r u), e = alpha/2 when 2r <= 3nu/2
+                   (the absolute term Lemmas 1, 2, 4 allow for a subnormal
+                   norm) and 0 otherwise; None if r^ is not finite
       sin_u        |sin phi| / u, phi the angle between x^ and x (Lemma 1)
       ulp          max_k |x^_k - x_k/r| / ulp(x_k/r)  (per component)."""
     xs = [fr(v) for v in x]
@@ -272,7 +273,8 @@ def errors(x, yhat, rhat, fmt: Fmt) -> dict:
     sin2 = (s * A - P * P) / (s * A) if A > 0 else Fr(1)
     sin_u = math.sqrt(max(float(sin2), 0.0)) / float(u)
     rh = float(rhat)
-    norm_u = float(abs(fr(rh) - r) / r / u) if math.isfinite(rh) else None
+    e = fmt.alpha / 2 if 16 * s <= 9 * fmt.nu ** 2 else Fr(0)
+    norm_u = float(max(abs(fr(rh) - r) - e, Fr(0)) / r / u) if math.isfinite(rh) else None
     ulp = 0.0
     for xk, yk in zip(xs, ys):
         ex = xk / r

@@ -177,7 +177,12 @@ def normalize_backward(y, g, saved_h, saved_code, offsets=None, *, out=None, pla
 class NormalizeFn(torch.autograd.Function):
     """y = x/|x| with the scaling algorithms, differentiable: the forward saves
     y, h = 1/r~ and the factor code; the backward kernel reads y, g and the
-    saved state once (x is not read again)."""
+    saved state once (x is not read again).
+
+    It always uses the vector zero rule (NGB_VECTOR_SEMANTICS): a dense
+    four-component zero input gives y = 0, not the quaternion (0, 0, 1, 0)
+    that normalize() returns without the flag.  Either zero result is a
+    constant, and the gradient at a zero input is +0."""
 
     @staticmethod
     def forward(ctx, x, offsets=None, plan=None):

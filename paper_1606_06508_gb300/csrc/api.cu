@@ -326,7 +326,7 @@ ngb_status ngb_plan_autotune(ngb_plan* p, const int64_t* offsets, const char* ca
   if (p->count == 0) return NGB_OK;
   cudaStream_t s = cs(stream);
   std::vector<int64_t> off((size_t)p->count + 1);
-  cudaError_t e = cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * off.size(), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(e, "autotune offsets read");
   for (int64_t i = 0; i < p->count; ++i)
