@@ -19,8 +19,10 @@ short secondary measurements of the other workloads.
 (per-workload evidence and profiling): fwdbwd_quat, rows_f32, rows_f64,
 ragged_f32, ragged_f64, fwdbwd_ragged_f64, vec3_f64, quat_f64.
 
-With N > 1 (torchrun) each rank normalizes its own batch (weak scaling, no
-data exchange); the timing is the max over ranks.
+With N > 1 (torchrun) the ranks share one global batch, each normalizing its
+contiguous shard (paper_1606_06508_gb300/shard.py; ragged shards balanced by
+element count): strong scaling with no data exchange, the timing the max over
+ranks.  --scaling weak gives every rank its own full-size batch instead.
 
 --impl reference times the oracle (plain single-threaded C, run on all host
 cores over contiguous vector ranges) on bounded samples of the same workload.
@@ -409,36 +411,65 @@ def dp_roofline(w, ms_per_step, rate):
             "peak_source": "measured live: ngb_fp64_probe (dmul + dadd chains)"}
 
 
-def build_work(name, count, rank, torch, L, api, synth, mapping=None):
+def _dense_shard(t, part):
+    """Rows [a, b) of t for part = (world, rank) (shard.dense_range); t itself
+    without a part."""
+    if part is None:
+        return t
+    from paper_1606_06508_gb300 import shard
+    a, b = shard.dense_range(t.shape[0], *part)
+    return t[a:b].contiguous()
+
+
+def _ragged_shard(off, tensors, part):
+    """The vectors [a, b) of a ragged batch for part = (world, rank), balanced
+    by element count (shard.ragged_range): their offsets rebased to 0 and the
+    slices of the packed arrays."""
+    if part is None:
+        return off, tensors
+    from paper_1606_06508_gb300 import shard
+    offh = off.cpu().numpy()
+    a, b = shard.ragged_range(offh, *part)
+    s0, s1 = int(offh[a]), int(offh[b])
+    return (off[a:b + 1] - s0).contiguous(), [t[s0:s1].contiguous() for t in tensors]
+
+
+def build_work(name, count, rank, torch, L, api, synth, mapping=None, part=None):
     """The workload `name`: its arrays (device tensors), `launch(p)` running
     one step of library calls on the pointers p[name] (so that the same step
     runs on device buffers or, for the end-to-end figure, on pinned host
     buffers), which arrays are the step's inputs and results, its units and
-    algorithmic bytes, and the post-timing checks."""
+    algorithmic bytes, and the post-timing checks.  With part = (world, rank)
+    every rank draws the same global batch and keeps its shard of it (strong
+    scaling, no exchange between ranks); otherwise each rank draws its own
+    full-size batch (weak scaling)."""
     dev = torch.device("cuda", torch.cuda.current_device())
     s = torch.cuda.current_stream()
-    seed = 1000 * rank
+    seed = 0 if part is not None else 1000 * rank
 
     if name == "quat":
-        x = synth.quaternions_f32_torch(count, seed=1 + seed, device=dev)
+        x = _dense_shard(synth.quaternions_f32_torch(count, seed=1 + seed, device=dev), part)
         y = torch.empty_like(x)
+        nq = x.shape[0]
 
         def launch(p):
-            st = L.normalize_f32(p["x"], p["y"], None, None, None, count, 4, None, None, 0, s.cuda_stream)
+            st = L.normalize_f32(p["x"], p["y"], None, None, None, nq, 4, None, None, 0, s.cuda_stream)
             if st:
                 L.check(st, "normalize_f32")
         return Work(desc=("2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 "
                           "wide-exponent/N(0,1) components") if count == QUAT_COUNT
                     else f"{count} binary32 quaternions, forward (profiling size)",
-                    units=count, bytes=32 * count, dtype="f32", kernel="k_small_vec16<float,4>", launches=1,
+                    units=nq, global_units=count, bytes=32 * nq, dtype="f32", kernel="k_small_vec16<float,4>",
+                    launches=1,
                     arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
                     parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="16 B read + 16 B written per quaternion")
 
     if name == "fwdbwd_quat":
-        n = count if count != QUAT_COUNT else 1 << 24
-        x = synth.quaternions_f32_torch(n, seed=4 + seed, device=dev)
-        g = synth.normal_like_torch((n, 4), torch.float32, seed=40 + seed, device=dev)
+        n_glob = count if count != QUAT_COUNT else 1 << 24
+        x = _dense_shard(synth.quaternions_f32_torch(n_glob, seed=4 + seed, device=dev), part)
+        g = _dense_shard(synth.normal_like_torch((n_glob, 4), torch.float32, seed=40 + seed, device=dev), part)
+        n = x.shape[0]
         y, gr = torch.empty_like(x), torch.empty_like(x)
         h = torch.empty(n, device=dev)
         c = torch.empty(n, dtype=torch.int8, device=dev)
@@ -448,7 +479,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
             L.check(L.normalize_backward_f32(p["y"], p["g"], p["h"], p["c"], p["gr"], n, 4, None, None, 0,
                                              s.cuda_stream), "bwd")
         return Work(desc=f"{n} binary32 quaternions, forward (saving h and code) + backward",
-                    units=n, bytes=90 * n, dtype="f32", kernel="k_small_vec16<float,4> + k_small_bwd<float,4>",
+                    units=n, global_units=n_glob, bytes=90 * n, dtype="f32",
+                    kernel="k_small_vec16<float,4> + k_small_bwd<float,4>",
                     launches=2, arrays={"x": x, "g": g, "y": y, "h": h, "c": c, "gr": gr}, inputs=["x", "g"],
                     results=["gr"], launch=launch,
                     parity=lambda: parity_full(x, y, 4, grad=gr, g=g), accuracy=lambda: accuracy_report(x, y, 4),
@@ -456,15 +488,16 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
 
     if name in ("rows_f32", "rows_f64"):
         dt = torch.float32 if name.endswith("f32") else torch.float64
-        rows = count if count != QUAT_COUNT else (1 << 20 if dt == torch.float32 else 1 << 19)
-        x = synth.rows_torch(rows, 256, dt, seed=2 + seed, device=dev)
+        rows_glob = count if count != QUAT_COUNT else (1 << 20 if dt == torch.float32 else 1 << 19)
+        x = _dense_shard(synth.rows_torch(rows_glob, 256, dt, seed=2 + seed, device=dev), part)
+        rows = x.shape[0]
         y = torch.empty_like(x)
         fn = L.normalize_f32 if dt == torch.float32 else L.normalize_f64
 
         def launch(p):
             L.check(fn(p["x"], p["y"], None, None, None, rows, 256, None, None, 0, s.cuda_stream), "rows")
         return Work(desc=f"{rows} rows of 256 {name[-3:]}, forward, N(0,1) x 2^s per row",
-                    units=rows, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
+                    units=rows, global_units=rows_glob, bytes=2 * x.numel() * x.element_size(), dtype=name[-3:],
                     kernel=('k_rows_half<4>' if dt == torch.float32 else 'k_rows_stream_batch<double,4>'), launches=1,
                     arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
                     parity=lambda: parity_full(x, y, 256), accuracy=lambda: accuracy_report(x, y, 256),
@@ -474,11 +507,15 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
     if name in ("ragged_f32", "ragged_f64", "fwdbwd_ragged_f64"):
         dt = torch.float64 if "f64" in name else torch.float32
         fb = name.startswith("fwdbwd")
-        cnt = count if count != QUAT_COUNT else (500_000 if fb else 4_000_000)
+        cnt_glob = count if count != QUAT_COUNT else (500_000 if fb else 4_000_000)
         kind, nmax = ("loguniform", 1024) if fb else ("mixture", 4096)
-        lengths = synth.ragged_lengths_torch(cnt, seed=3 + seed, kind=kind, nmax=nmax, device=dev)
+        lengths = synth.ragged_lengths_torch(cnt_glob, seed=3 + seed, kind=kind, nmax=nmax, device=dev)
         off = synth.offsets_from_lengths_torch(lengths)
         x = synth.ragged_values_torch(lengths, dt, seed=3 + seed)
+        g = synth.normal_like_torch(x.shape, dt, seed=41 + seed, device=dev) if fb else None
+        off, parts = _ragged_shard(off, [x, g] if fb else [x], part)
+        x, g = (parts[0], parts[1]) if fb else (parts[0], None)
+        cnt = off.numel() - 1
         y = torch.empty_like(x)
         plan = api.Plan(cnt, dt)
         if mapping:  # a fixed mapping (profiling): no autotuning launches before the timed ones
@@ -494,14 +531,14 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                         "ragged")
             return Work(desc=f"{cnt} ragged {name[-3:]} vectors (40% of length 2-4, else log-uniform [5,4096]), "
                              f"int64 offsets, forward, one persistent launch after the classifier",
-                        units=cnt, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1), dtype=name[-3:],
+                        units=cnt, global_units=cnt_glob, bytes=2 * x.numel() * s_bytes + 8 * (cnt + 1),
+                        dtype=name[-3:],
                         kernel="k_classify + k_ragged (persistent)", launches=2,
                         arrays={"x": x, "off": off, "y": y}, inputs=["x", "off"], results=["y"], launch=launch,
                         parity=lambda: parity_full(x, y, 0, off=off), accuracy=lambda: accuracy_report(x, y, 0, off=off),
                         mapping=list(mapping), plan=plan,
                         bytes_model="2 n s per vector + 8 B offsets",
                         dp_ops=(3 * x.numel() + 3 * cnt) if dt == torch.float64 else None)
-        g = synth.normal_like_torch(x.shape, dt, seed=41 + seed, device=dev)
         gr = torch.empty_like(x)
         h = torch.empty(cnt, dtype=dt, device=dev)
         c = torch.empty(cnt, dtype=torch.int8, device=dev)
@@ -511,7 +548,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
             L.check(L.normalize_backward_f64(p["y"], p["g"], p["h"], p["c"], p["gr"], cnt, 0, p["off"], plan.handle, 0,
                                              s.cuda_stream), "bwd")
         return Work(desc=f"{cnt} ragged binary64 vectors, lengths log-uniform [2,1024], forward + backward",
-                    units=cnt, bytes=5 * x.numel() * s_bytes + 2 * 9 * cnt + 2 * 8 * (cnt + 1), dtype="f64",
+                    units=cnt, global_units=cnt_glob, bytes=5 * x.numel() * s_bytes + 2 * 9 * cnt + 2 * 8 * (cnt + 1),
+                    dtype="f64",
                     kernel="k_classify + k_ragged; k_classify + k_ragged_bwd_{blocks,warps,threads}", launches=6,
                     arrays={"x": x, "g": g, "off": off, "y": y, "h": h, "c": c, "gr": gr},
                     inputs=["x", "g", "off"], results=["gr"], launch=launch,
@@ -522,28 +560,31 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None):
                     dp_ops=8 * x.numel() + 3 * cnt)
 
     if name == "quat_f64":
-        n = count if count != QUAT_COUNT else 1 << 25
-        x = synth.quaternions_f64_torch(n, seed=5 + seed, device=dev)
+        n_glob = count if count != QUAT_COUNT else 1 << 25
+        x = _dense_shard(synth.quaternions_f64_torch(n_glob, seed=5 + seed, device=dev), part)
+        n = x.shape[0]
         y = torch.empty_like(x)
 
         def launch(p):
             L.check(L.normalize_f64(p["x"], p["y"], None, None, None, n, 4, None, None, 0, s.cuda_stream), "quat_f64")
         return Work(desc=f"{n} binary64 quaternions (components sign x U[1,2) x 2^e, e in [-30,30]), forward",
-                    units=n, bytes=64 * n, dtype="f64", kernel="k_small_direct<double,4>", launches=1,
+                    units=n, global_units=n_glob, bytes=64 * n, dtype="f64", kernel="k_small_direct<double,4>",
+                    launches=1,
                     arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
                     parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
                     bytes_model="32 B read + 32 B written per quaternion", dp_ops=15 * n)
 
     if name == "vec3_f64":
         xh = synth.vectors3_f64(65536, seed=0 + seed)
-        x = torch.from_numpy(xh).to(dev)
+        x = _dense_shard(torch.from_numpy(xh).to(dev), part)
         y = torch.empty_like(x)
         cnt = x.shape[0]
 
         def launch(p):
             L.check(L.normalize_f64(p["x"], p["y"], None, None, None, cnt, 3, None, None, 0, s.cuda_stream), "vec3")
         return Work(desc="65,536 x 3 binary64 vectors (e in [-30,30]) + 64 edge vectors, forward",
-                    units=cnt, bytes=48 * cnt, dtype="f64", kernel="k_small_direct<double,3>", launches=1,
+                    units=cnt, global_units=xh.shape[0], bytes=48 * cnt, dtype="f64",
+                    kernel="k_small_direct<double,3>", launches=1,
                     arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
                     parity=lambda: parity_full(x, y, 3), accuracy=lambda: accuracy_report(x, y, 3, k=4000),
                     flush=True, bytes_model="24 B read + 24 B written per vector", dp_ops=12 * cnt)
@@ -672,7 +713,7 @@ def run_reference(args):
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "vectors/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "higher_is_better": True, "scaling": args.scaling, "vs_baseline": None,
         "dtype": "f64" if args.workload.endswith("f64") else "f32", "data": "synthetic",
         "config": {"workload": full_size_desc(args.workload), "workload_name": args.workload,
                    "reference_step": f"{units} vectors of the same recipe (bounded sample)"},
@@ -704,7 +745,11 @@ def run_ours(args):
 
     peak, peak_src = peaks()
     s = torch.cuda.current_stream()
-    w = build_work(args.workload, args.count, rank, torch, L, api, synth, mapping=args.mapping)
+    strong = args.scaling == "strong"
+    w = build_work(args.workload, args.count, rank, torch, L, api, synth, mapping=args.mapping,
+                   part=(world, rank) if strong and world > 1 else None)
+    # units all ranks process per step: the global batch (strong), or world full batches (weak)
+    job_units = w.global_units if strong else world * w.units
     flush = None
     if w.flush:
         flush_buf = torch.empty(2 * L2_BYTES // 4, device=dev)
@@ -753,16 +798,18 @@ def run_ours(args):
         achieved = w.bytes / step_s / 1e9
         traffic, tnote = traffic_for(args.workload)
         result = {
-            "metric": METRIC, "value": world * args.steps * w.units / secs, "unit": "vectors/s", "n_gpus": world,
+            "metric": METRIC, "value": args.steps * job_units / secs, "unit": "vectors/s", "n_gpus": world,
             "steps": args.steps, "warmup": warm, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
+            "scaling": args.scaling, "vs_baseline": None, "dtype": w.dtype, "data": "synthetic",
             "config": {"workload": full_size_desc(args.workload) if args.count == QUAT_COUNT else w.desc,
                        "workload_name": args.workload,
                        "vectors_per_gpu": w.units, "algorithmic_bytes_per_step_per_gpu": w.bytes,
                        "bytes_model": w.bytes_model,
                        "l2": ("L2 flushed between steps (256 MB write), outside the timed intervals" if w.flush else
                               "inputs larger than L2 (126 MB); no flush"),
-                       "parallelism": f"independent batch per GPU x{world}",
+                       "parallelism": (f"one global batch of {w.global_units} vectors sharded over {world} GPU(s) by "
+                                       "contiguous vector ranges (ragged: balanced by element count), no exchange"
+                                       if strong else f"independent full-size batch per GPU x{world}"),
                        **({"mapping": w.mapping} if hasattr(w, "mapping") else {})},
             "GB_per_s": world * args.steps * w.bytes / secs / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -841,7 +888,7 @@ def run_ours(args):
     if rank == 0:
         h2d = sum(host[k].numel() * host[k].element_size() for k in w.inputs)
         d2h = sum(host[k].numel() * host[k].element_size() for k in w.results)
-        result["e2e"] = {"value": world * e2e_steps * w.units / (zms * 1e-3), "unit": "vectors/s",
+        result["e2e"] = {"value": e2e_steps * job_units / (zms * 1e-3), "unit": "vectors/s",
                          "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                          "ms_per_step": zms / e2e_steps,
                          "link_GB_per_s": (h2d + d2h) * e2e_steps / (zms * 1e-3) / 1e9,
@@ -849,7 +896,7 @@ def run_ours(args):
                                  "and their kernels read the inputs and write the results over the host link "
                                  "(zero-copy), inside every timed step",
                          "results_equal_device_path": bool(same),
-                         "staged": {"value": world * e2e_steps * w.units / (sms * 1e-3), "unit": "vectors/s",
+                         "staged": {"value": e2e_steps * job_units / (sms * 1e-3), "unit": "vectors/s",
                                     "ms_per_step": sms / e2e_steps,
                                     "note": "copy engines: pinned host inputs -> device, the device call(s), device "
                                             "results -> pinned host, one after the other"}}
@@ -877,6 +924,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=WORKLOAD_NAMES, default="quat")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--scaling", choices=["strong", "weak"], default="strong",
+                    help="with N > 1: strong = every rank takes its shard of one global batch (shard.py ranges, no "
+                         "exchange); weak = every rank normalizes its own full-size batch")
     ap.add_argument("--kernels-only", action="store_true",
                     help="profiling: time the steps and print the line without the end-to-end figure, the checks "
                          "and the CPU baseline")

@@ -12,6 +12,9 @@
 //   padded  binary64: the components zero-padded to 4 and the integer-pipe
 //           form for n <= 4 when in range, else normalize_small_hw (the
 //           ragged kernel's thread items)
+//   sq64    binary64: the integer-pipe form with the squares on the FP64
+//           pipe (the dense kernels' choice for warps that are all in range)
+//           when in range, else normalize_small_hw
 //   quot1, quot2  dim 3: the quotient Algorithms 1 and 2 (ngb_quotient.cuh);
 //           h and code are written as zero
 // Mode bwd reads y, g (count x dim each), h (count) and code (count bytes)
@@ -49,6 +52,15 @@ static int fwd_small(const T* x, T* y, T& r, T& h, bool qz, const char* mode) {
     exit(2);
   }
   if (!strcmp(mode, "hw")) return normalize_small_hw<T, D>(x, y, r, h, qz);
+  if (!strcmp(mode, "sq64")) {
+    if constexpr (sizeof(T) == 8) {
+      const SmallKeysF64<D> kk(x);
+      if (kk.ok) return normalize_small_f64_int<D>(x, y, r, h, qz, kk, true);
+      return normalize_small_hw<T, D>(x, y, r, h, qz);
+    }
+    fprintf(stderr, "sq64 is a binary64 mode\n");
+    exit(2);
+  }
   if (!strcmp(mode, "padded")) {
     if constexpr (sizeof(T) == 8) {
       double xv[4] = {0, 0, 0, 0}, yv[4];

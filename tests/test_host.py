@@ -154,7 +154,10 @@ def _gloo_worker(rank, world, port, q):
     if rank == 0:
         full = np.concatenate([p[2] for p in sorted(parts, key=lambda t: t[0])])
         ref = oracle.normalize(x, dim=0, offsets=off)[0]
-        q.put(bool(np.array_equal(full, ref)) and parts[0][1] == parts[1][0])
+        # each shard's element count is within one vector's length of an even split
+        elems = [int(off[b_] - off[a_]) for a_, b_, _ in parts]
+        balanced = all(abs(e - int(off[-1]) / world) <= int(lengths.max()) for e in elems)
+        q.put(bool(np.array_equal(full, ref)) and parts[0][1] == parts[1][0] and balanced)
     dist.barrier()
     dist.destroy_process_group()
 
@@ -175,3 +178,31 @@ def test_gloo_two_ranks_shard_and_gather():
         p.join(120)
     assert all(p.exitcode == 0 for p in procs)
     assert q.get(timeout=5) is True
+
+
+def test_bench_shards_partition_one_global_batch():
+    """bench.py's strong-scaling shards (the ranges of shard.py): the ranks'
+    slices concatenate to the global batch, each ragged shard's offsets start
+    at 0 and describe its slice, and element counts stay within one vector's
+    length of an even split."""
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1606_06508_gb300 import synth
+    x = torch.arange(1001 * 4, dtype=torch.float32).reshape(1001, 4)
+    lengths = synth.ragged_lengths(5000, seed=3)
+    off = torch.from_numpy(synth.offsets_from_lengths(lengths))
+    v = torch.arange(int(off[-1]), dtype=torch.float64)
+    g = -v
+    for world in (1, 2, 3, 8):
+        parts = [bench._dense_shard(x, (world, r)) for r in range(world)]
+        assert torch.equal(torch.cat(parts), x)
+        vs, gs = [], []
+        for r in range(world):
+            o, (vr, gr) = bench._ragged_shard(off, [v, g], (world, r))
+            assert int(o[0]) == 0 and int(o[-1]) == vr.numel() == gr.numel()
+            assert abs(vr.numel() - int(off[-1]) / world) <= int(lengths.max())
+            vs.append(vr)
+            gs.append(gr)
+        assert torch.equal(torch.cat(vs), v) and torch.equal(torch.cat(gs), g)
+    assert bench._dense_shard(x, None) is x

@@ -3,7 +3,8 @@ through tests/kernel_host_check.cpp, the CUDA intrinsics mapped to the host's
 IEEE operations by tests/hostcuda/cuda_runtime.h) against the oracle, bit for
 bit, on CPU: the n <= 4 forward in its integer-pipe and hardware forms, the
 zero-padded form of the ragged thread items, the generic thread path for
-5 <= n <= 16, the backward, and the quotient Algorithms 1 and 2.  The GPU parity tests check the same code on
+5 <= n <= 16, the backward, the binary64 form with the squares on the FP64
+pipe, and the quotient Algorithms 1 and 2.  The GPU parity tests check the same code on
 the device; this catches a mistake in the arithmetic without one."""
 import os
 import shutil
@@ -91,7 +92,7 @@ def _inputs(f, dim, seed):
 @pytest.mark.parametrize("f", ["f32", "f64"])
 @pytest.mark.parametrize("dim", [1, 2, 3, 4])
 def test_small_forward_matches_oracle(khc, f, dim):
-    modes = ["fwd", "hw"] + (["padded"] if f == "f64" else [])
+    modes = ["fwd", "hw"] + (["padded", "sq64"] if f == "f64" else [])
     for k, x in enumerate(_inputs(f, dim, seed=40 + dim)):
         for mode in modes:  # ragged thread items keep the vector zero rule for n = 4
             _check_forward(khc, x, dim, mode, flags=1 if mode == "padded" else 0, what=f"{f} d={dim} set {k} {mode}")
