@@ -124,7 +124,8 @@ ngb_status normalize_backward_f64(const double* y, const double* g, const double
                                   const int64_t* offsets, ngb_plan* plan, uint32_t flags, ngb_stream_t stream);
 
 /*
- * Ragged plans.  A plan holds the device work lists (12 bytes per vector plus
+ * Ragged plans.  A plan holds the device work lists (12 bytes per vector in
+ * binary32, 20 in binary64, which has two more length classes, plus
  * a few counters) for ragged batches of exactly `count` vectors of one dtype
  * (dtype_bytes 4 or 8), the thread/warp/block mapping, and the CUDA graphs
  * that replay the two launches of a call.  It is bound to count and dtype,

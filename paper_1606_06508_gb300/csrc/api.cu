@@ -59,7 +59,7 @@ struct ngb_plan {
   int32_t dtype_bytes = 0;
   int64_t capacity = 0;
   int device = 0;
-  int32_t* buf = nullptr;  // counts[3], tickets[3], status, pad, items[3 * count]
+  int32_t* buf = nullptr;  // scratch header, then the work lists (ngb::ragged_scratch)
   ngb::RaggedScratch sc{};
   ngb::RaggedMapping map{8, 8192, 256, 0};
   bool graphs = true;
@@ -223,17 +223,15 @@ ngb_status ngb_plan_create(ngb_plan** out, int64_t count, int32_t dtype_bytes, i
   p->dtype_bytes = dtype_bytes;
   p->capacity = capacity;
   cudaError_t e = cudaGetDevice(&p->device);
-  if (e == cudaSuccess) e = cudaMalloc(&p->buf, sizeof(int32_t) * (size_t)(8 + 3 * count));
-  if (e == cudaSuccess) e = cudaMemset(p->buf, 0, sizeof(int32_t) * 8);
+  const size_t words = ngb::SCRATCH_HEADER_WORDS + (size_t)ngb::ragged_lists(dtype_bytes) * (size_t)count;
+  if (e == cudaSuccess) e = cudaMalloc(&p->buf, sizeof(int32_t) * words);
+  if (e == cudaSuccess) e = cudaMemset(p->buf, 0, sizeof(int32_t) * ngb::SCRATCH_HEADER_WORDS);
   if (e != cudaSuccess) {
     if (p->buf) cudaFree(p->buf);
     delete p;
     return cuda_fail(e, "ngb_plan_create");
   }
-  p->sc.counts = p->buf;
-  p->sc.tickets = p->buf + 3;
-  p->sc.status = p->buf + 6;
-  p->sc.items = p->buf + 8;
+  p->sc = ngb::ragged_scratch(p->buf);
   *out = p;
   return NGB_OK;
 }

@@ -33,38 +33,61 @@ constexpr bool ROWS_HALF_WARP = true;
 
 // ---------------------------------------------------------------------------
 // dim <= 4, one 16-byte vector per thread, U vectors in flight per thread.
-// The loops run over warp-aligned ranges (lane = index within the warp), so
-// that every lane of a warp reaches normalize_small_warp together; lanes past
-// the end load zeros and write nothing.
+// binary32: a grid-stride loop per lane.  binary64: the loop runs over
+// warp-aligned ranges (lane = index within the warp), so that every lane of a
+// warp reaches normalize_small_warp together; lanes past the end load zeros
+// and write nothing.  (The warp-aligned form cost the binary32 quaternion
+// kernel 2 % of its bandwidth, which needs no vote: it is kept per lane.)
 template <typename T, int D>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_vec16(const T* __restrict__ x, T* y, VecOut<T> out,
                                                                 int64_t count, int quat_zero) {
   static_assert(D * sizeof(T) == 16, "one 16-byte vector per element vector");
   constexpr int U = VEC16_IN_FLIGHT;
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); w0 < count; w0 += stride * U) {
-    const int64_t i0 = w0 + lane;
-    T xv[U][D];
+  if constexpr (sizeof(T) == 4) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+      T xv[U][D];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
-      if (i < count) {
-        Vec<T, D>::load(x + i * D, xv[u]);
-      } else {
-#pragma unroll
-        for (int k = 0; k < D; ++k) xv[u][k] = T(0);
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < count) Vec<T, D>::load(x + i * D, xv[u]);
       }
-    }
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
-      if (w0 + u * stride < count) {  // warp-uniform
-        T yv[D], r, h;
-        const int code = normalize_small_warp<T, D>(xv[u], yv, r, h, quat_zero != 0, i < count);
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
         if (i < count) {
+          T yv[D], r, h;
+          const int code = normalize_small<T, D>(xv[u], yv, r, h, quat_zero != 0);
           if (y) Vec<T, D>::store(y + i * D, yv);
           out.put(i, r, h, code);
+        }
+      }
+    }
+  } else {
+    const int lane = threadIdx.x & 31;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); w0 < count; w0 += stride * U) {
+      const int64_t i0 = w0 + lane;
+      T xv[U][D];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < count) {
+          Vec<T, D>::load(x + i * D, xv[u]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < D; ++k) xv[u][k] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (w0 + u * stride < count) {  // warp-uniform
+          T yv[D], r, h;
+          const int code = normalize_small_warp<T, D>(xv[u], yv, r, h, quat_zero != 0, i < count);
+          if (i < count) {
+            if (y) Vec<T, D>::store(y + i * D, yv);
+            out.put(i, r, h, code);
+          }
         }
       }
     }
@@ -81,29 +104,56 @@ template <typename T, int D>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_direct(const T* __restrict__ x, T* y, VecOut<T> out,
                                                                  int64_t count, int quat_zero) {
   constexpr int U = sizeof(T) == 8 ? 1 : 4;
-  const int lane = threadIdx.x & 31;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); w0 < count; w0 += stride * U) {
-    const int64_t i0 = w0 + lane;
-    T xv[U][D];
+  if constexpr (sizeof(T) == 4) {
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+      T xv[U][D];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
-#pragma unroll
-      for (int k = 0; k < D; ++k) xv[u][k] = i < count ? __ldcs(x + i * D + k) : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
-      if (w0 + u * stride < count) {  // warp-uniform
-        T yv[D], r, h;
-        const int code = normalize_small_warp<T, D>(xv[u], yv, r, h, quat_zero != 0, i < count);
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
         if (i < count) {
+#pragma unroll
+          for (int k = 0; k < D; ++k) xv[u][k] = __ldcs(x + i * D + k);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < count) {
+          T yv[D], r, h;
+          const int code = normalize_small<T, D>(xv[u], yv, r, h, quat_zero != 0);
           if (y) {
 #pragma unroll
             for (int k = 0; k < D; ++k) __stcs(y + i * D + k, yv[k]);
           }
           out.put(i, r, h, code);
+        }
+      }
+    }
+  } else {  // warp-aligned ranges, as in k_small_vec16
+    const int lane = threadIdx.x & 31;
+    for (int64_t w0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); w0 < count; w0 += stride * U) {
+      const int64_t i0 = w0 + lane;
+      T xv[U][D];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+#pragma unroll
+        for (int k = 0; k < D; ++k) xv[u][k] = i < count ? __ldcs(x + i * D + k) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (w0 + u * stride < count) {  // warp-uniform
+          T yv[D], r, h;
+          const int code = normalize_small_warp<T, D>(xv[u], yv, r, h, quat_zero != 0, i < count);
+          if (i < count) {
+            if (y) {
+#pragma unroll
+              for (int k = 0; k < D; ++k) __stcs(y + i * D + k, yv[k]);
+            }
+            out.put(i, r, h, code);
+          }
         }
       }
     }

@@ -4,39 +4,52 @@
 //
 // 1. k_classify reads the int64 offsets once, skips (and flags) vectors with
 //    bad offsets, finishes zero-length vectors (norm +0), and appends every
-//    other vector index to one of three lists by length: the block list
-//    (n > warp_max), the warp list (thread_max < n <= warp_max) and the thread
-//    list (n <= thread_max; n <= 4 always).  Appends are aggregated per block:
-//    one atomic per block and list.
+//    other vector index to one of the lists by length: the block list
+//    (n > warp_max), the warp list (thread_max < n <= warp_max), in binary64
+//    two group lists for the shorter warp-sized vectors (n <= 64: groups of
+//    8 lanes; n <= 128: groups of 16 lanes; csrc/ngb_grouppath.cuh), and the
+//    thread list (n <= thread_max; n <= 4 always).  Appends are aggregated
+//    per block: one atomic per block and list.
 // 2. Forward: k_ragged runs one wave of persistent blocks that take work from
-//    the three lists in that order (longest vectors first) through atomic
-//    tickets: whole blocks on block items, warps on batches of warp items,
-//    lanes on thread items.  Warps and blocks stream their vector (three
-//    passes, a few partial sums per lane) instead of holding it, so the
-//    kernel keeps few registers and many loads in flight; in binary32 a warp
-//    prefetches its next item into L2 while it works on the current one.  No
-//    block ever waits for another.
+//    the lists, longest vectors first, through atomic tickets: whole blocks
+//    on block items, warps on batches of warp items, groups of lanes on group
+//    items, lanes on thread items.  Warps and blocks stream their vector
+//    (three passes, a few partial sums per lane) instead of holding it, so
+//    the kernel keeps few registers and many loads in flight; in binary32 a
+//    warp prefetches its next item into L2 while it works on the current one.
+//    Groups hold their (short) vector in registers.  No block ever waits for
+//    another.
 // 3. Backward: one plain grid-stride kernel per list (k_ragged_bwd_blocks,
-//    k_ragged_bwd_warps, k_ragged_bwd_threads).
+//    k_ragged_bwd_warps, k_ragged_bwd_groups, k_ragged_bwd_threads).
 // Every mapping evaluates the same operations in the same order (the paper's
 // Algorithms 3-7 for n <= 4, the order CR(n) for n >= 5), so the results do
 // not depend on the mapping, the grid or the order in which items are taken.
 #pragma once
 #include "ngb_internal.h"
-#include "ngb_rowpath.cuh"
+#include "ngb_grouppath.cuh"
 
 namespace ngb {
 
 constexpr int CLASSIFY_THREADS = 1024;
 constexpr int WARP_BATCH = 4;     // warp items per ticket (binary32 ragged: 4 0.847, 8 0.843, 16 0.825)
 constexpr int THREAD_BATCH = 4;   // 32-item groups per ticket
+constexpr int GROUP_BATCH = 4;    // rounds of 32 / W group items per ticket
+
+// The longest vectors of the group lists (0: no group list).  binary64
+// only: there the per-vector steps run on the scarce FP64 pipe, and a group
+// of W lanes shares each of their instructions among 32 / W vectors.
+template <typename T> __host__ __device__ constexpr int group8_max() { return sizeof(T) == 8 ? 64 : 0; }
+template <typename T> __host__ __device__ constexpr int group16_max() { return sizeof(T) == 8 ? 128 : 0; }
+static_assert(ragged_lists(4) == 3 && group8_max<float>() == 0 && group16_max<float>() == 0,
+              "binary32 scratch holds three lists");
+static_assert(ragged_lists(8) == NLISTS, "binary64 scratch holds every list");
 
 template <typename T>
 __global__ void __launch_bounds__(CLASSIFY_THREADS)
     k_classify(const int64_t* __restrict__ off, int64_t count, int64_t capacity, int thread_max, int warp_max,
                int validate, RaggedScratch sc, VecOut<T> zero_out) {
-  __shared__ int wcount[CLASSIFY_THREADS / 32][3];
-  __shared__ int wbase[CLASSIFY_THREADS / 32][3];
+  __shared__ int wcount[CLASSIFY_THREADS / 32][NLISTS];
+  __shared__ int wbase[CLASSIFY_THREADS / 32][NLISTS];
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const unsigned lt_mask = (1u << lane) - 1u;
   for (int64_t base = (int64_t)blockIdx.x * CLASSIFY_THREADS; base < count;
@@ -56,12 +69,16 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
         zero_out.put(i, T(0), T(0), CODE_ZERO);
       } else {
         // n <= 4 always runs Algorithms 5-7 in one thread
-        b = (n <= thread_max || n <= 4) ? 2 : (n <= warp_max ? 1 : 0);
+        if (n <= thread_max || n <= 4) b = LIST_THREAD;
+        else if (n > warp_max) b = LIST_BLOCK;
+        else if (n <= group8_max<T>()) b = LIST_GROUP8;
+        else if (n <= group16_max<T>()) b = LIST_GROUP16;
+        else b = LIST_WARP;
       }
     }
-    unsigned ball[3];
+    unsigned ball[NLISTS];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < NLISTS; ++k) {
       ball[k] = __ballot_sync(FULL, b == k);
       if (lane == 0) wcount[w][k] = __popc(ball[k]);
     }
@@ -69,7 +86,7 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
     if (w == 0) {  // per bucket: exclusive scan of the 32 warp counts by shuffles, one atomic per block
       static_assert(CLASSIFY_THREADS == 1024, "one warp count per lane");
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
+      for (int k = 0; k < NLISTS; ++k) {
         const int c = wcount[lane][k];
         int incl = c;
 #pragma unroll
@@ -85,7 +102,10 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
     }
     __syncthreads();
     if (b >= 0) {
-      const unsigned mine = b == 0 ? ball[0] : (b == 1 ? ball[1] : ball[2]);
+      unsigned mine = 0;
+#pragma unroll
+      for (int k = 0; k < NLISTS; ++k)
+        if (b == k) mine = ball[k];
       sc.items[(int64_t)b * count + wbase[w][b] + __popc(mine & lt_mask)] = (int32_t)i;
     }
     __syncthreads();
@@ -195,6 +215,31 @@ __device__ __forceinline__ void prefetch_item_l2(const RaggedArgs<T>& a, int64_t
 }
 
 
+// Group items of list `list`: each warp takes GROUP_BATCH rounds of 32 / W
+// items per ticket, one item per group of W lanes.
+template <typename T, int W>
+__device__ __forceinline__ void ragged_group_items(const RaggedArgs<T>& a, int list, int lane) {
+  constexpr int PER = 32 / W;
+  const int cnt = a.sc.counts[list];
+  const int32_t* L = a.sc.items + (int64_t)list * a.count;
+  for (;;) {
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&a.sc.tickets[list], PER * GROUP_BATCH);
+    base = __shfl_sync(FULL, base, 0);
+    if (base >= cnt) break;
+#pragma unroll 1
+    for (int j = 0; j < GROUP_BATCH; ++j) {
+      const int it = base + PER * j + lane / W;
+      if (it < cnt) {  // the same in every lane of a group
+        const int64_t vec = L[it];
+        const int64_t s = a.off[vec];
+        const int n = (int)(a.off[vec + 1] - s);
+        group_forward<T, W>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+      }
+    }
+  }
+}
+
 template <typename T>
 constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 3 * 256 / B; }
 
@@ -202,14 +247,14 @@ template <typename T, int B>
 __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
   const int t = threadIdx.x, lane = t & 31;
-  const int nblk = a.sc.counts[0], nwarp = a.sc.counts[1], nthr = a.sc.counts[2];
-  const int32_t* Lb = a.sc.items;
-  const int32_t* Lw = a.sc.items + a.count;
-  const int32_t* Lt = a.sc.items + 2 * a.count;
+  const int nblk = a.sc.counts[LIST_BLOCK], nwarp = a.sc.counts[LIST_WARP], nthr = a.sc.counts[LIST_THREAD];
+  const int32_t* Lb = a.sc.items + LIST_BLOCK * a.count;
+  const int32_t* Lw = a.sc.items + LIST_WARP * a.count;
+  const int32_t* Lt = a.sc.items + LIST_THREAD * a.count;
 
   // block items, one ticket per item
   for (;;) {
-    if (t == 0) sh.item = atomicAdd(&a.sc.tickets[0], 1);
+    if (t == 0) sh.item = atomicAdd(&a.sc.tickets[LIST_BLOCK], 1);
     __syncthreads();
     const int it = sh.item;
     __syncthreads();
@@ -224,7 +269,7 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
   // the next item of the ticket into L2 while the current item runs.
   for (;;) {
     int base = 0;
-    if (lane == 0) base = atomicAdd(&a.sc.tickets[1], WARP_BATCH);
+    if (lane == 0) base = atomicAdd(&a.sc.tickets[LIST_WARP], WARP_BATCH);
     base = __shfl_sync(FULL, base, 0);
     if (base >= nwarp) break;
     for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
@@ -237,10 +282,14 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
     }
   }
 
+  // group items (binary64): groups of 16, then of 8 lanes
+  if constexpr (group16_max<T>() > 0) ragged_group_items<T, 16>(a, LIST_GROUP16, lane);
+  if constexpr (group8_max<T>() > 0) ragged_group_items<T, 8>(a, LIST_GROUP8, lane);
+
   // thread items, THREAD_BATCH groups of 32 per ticket
   for (;;) {
     int base = 0;
-    if (lane == 0) base = atomicAdd(&a.sc.tickets[2], 32 * THREAD_BATCH);
+    if (lane == 0) base = atomicAdd(&a.sc.tickets[LIST_THREAD], 32 * THREAD_BATCH);
     base = __shfl_sync(FULL, base, 0);
     if (base >= nthr) break;
 #pragma unroll 1
@@ -260,8 +309,8 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
 template <typename T, int B>
 __global__ void __launch_bounds__(B) k_ragged_bwd_blocks(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
-  const int nblk = a.sc.counts[0];
-  const int32_t* Lb = a.sc.items;
+  const int nblk = a.sc.counts[LIST_BLOCK];
+  const int32_t* Lb = a.sc.items + LIST_BLOCK * a.count;
   for (int it = blockIdx.x; it < nblk; it += gridDim.x) {
     const int64_t vec = Lb[it];
     const int64_t s = a.off[vec];
@@ -274,8 +323,8 @@ __global__ void __launch_bounds__(B) k_ragged_bwd_blocks(RaggedArgs<T> a) {
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_ragged_bwd_warps(RaggedArgs<T> a) {
   const int lane = threadIdx.x & 31;
-  const int nwarp = a.sc.counts[1];
-  const int32_t* Lw = a.sc.items + a.count;
+  const int nwarp = a.sc.counts[LIST_WARP];
+  const int32_t* Lw = a.sc.items + LIST_WARP * a.count;
   const int w0 = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
   for (int it = w0; it < nwarp; it += nw) {
@@ -286,11 +335,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_ragged_bwd_warp
   }
 }
 
+// Backward, a group list: one group of W lanes per vector, 32 / W vectors per
+// warp, warp-stride over the list.
+template <typename T, int W>
+__global__ void __launch_bounds__(256) k_ragged_bwd_groups(RaggedArgs<T> a, int list) {
+  constexpr int PER = 32 / W;
+  const int lane = threadIdx.x & 31;
+  const int cnt = a.sc.counts[list];
+  const int32_t* L = a.sc.items + (int64_t)list * a.count;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t it0 = w0 * PER; it0 < cnt; it0 += nw * PER) {
+    const int64_t it = it0 + lane / W;
+    if (it < cnt) {  // the same in every lane of a group
+      const int64_t vec = L[it];
+      const int64_t s = a.off[vec];
+      const int n = (int)(a.off[vec + 1] - s);
+      group_backward<T, W>(a.x + s, a.g + s, a.y + s, n, lane, a.h_in[vec], a.c_in[vec]);
+    }
+  }
+}
+
 // Backward, thread list: one thread per vector, grid-stride over the list.
 template <typename T>
 __global__ void __launch_bounds__(256) k_ragged_bwd_threads(RaggedArgs<T> a) {
-  const int nthr = a.sc.counts[2];
-  const int32_t* Lt = a.sc.items + 2 * a.count;
+  const int nthr = a.sc.counts[LIST_THREAD];
+  const int32_t* Lt = a.sc.items + LIST_THREAD * a.count;
   const int stride = (int)((int64_t)gridDim.x * blockDim.x);
   for (int it = (int)((int64_t)blockIdx.x * blockDim.x + threadIdx.x); it < nthr; it += stride) {
     const int64_t vec = Lt[it];
@@ -324,6 +394,10 @@ inline void launch_backward_lists(const RaggedArgs<T>& a, const RaggedMapping& m
     k_ragged_bwd_blocks<T, 256><<<clamp(wave_of(k_ragged_bwd_blocks<T, 256>, 256)), 256, 0, s>>>(a);
   }
   k_ragged_bwd_warps<T><<<clamp(wave_of(k_ragged_bwd_warps<T>, 256)), 256, 0, s>>>(a);
+  if constexpr (group16_max<T>() > 0)
+    k_ragged_bwd_groups<T, 16><<<clamp(wave_of(k_ragged_bwd_groups<T, 16>, 256)), 256, 0, s>>>(a, LIST_GROUP16);
+  if constexpr (group8_max<T>() > 0)
+    k_ragged_bwd_groups<T, 8><<<clamp(wave_of(k_ragged_bwd_groups<T, 8>, 256)), 256, 0, s>>>(a, LIST_GROUP8);
   k_ragged_bwd_threads<T><<<clamp(wave_of(k_ragged_bwd_threads<T>, 256)), 256, 0, s>>>(a);
 }
 
@@ -339,7 +413,7 @@ cudaError_t launch_ragged_impl(const T* x, T* y, T* norm, T* saved_h, int8_t* sa
                                const int8_t* code_in, T* grad, const int64_t* offsets, int64_t count,
                                int64_t capacity, bool validate, const RaggedMapping& map, const RaggedScratch& sc,
                                bool backward, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(sc.counts, 0, 6 * sizeof(int32_t), s);  // counts and tickets are adjacent
+  cudaError_t e = cudaMemsetAsync(sc.counts, 0, 2 * NLISTS * sizeof(int32_t), s);  // counts, tickets: adjacent
   if (e != cudaSuccess) return e;
   {
     const int64_t blocks_needed = (count + CLASSIFY_THREADS - 1) / CLASSIFY_THREADS;

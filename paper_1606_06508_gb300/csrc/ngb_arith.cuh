@@ -413,7 +413,7 @@ struct SmallKeysF64 {
   }
 };
 
-// fp64_squares: form the squares x~_k^2 with the FP64 pipe's multiplication
+// FP64_SQUARES: form the squares x~_k^2 with the FP64 pipe's multiplication
 // instead of f64emu::square (the same bits: in this range every square is a
 // normal number, and both are the correctly rounded product).  Measured on
 // 2^25 binary64 quaternions whose components all lie in range: 0.85 ms
@@ -421,10 +421,9 @@ struct SmallKeysF64 {
 // where many vectors take the hardware steps and already load the FP64 pipe,
 // the FP64 squares were 7 % slower.  The dense kernels therefore choose them
 // per warp, when every vector of the warp is in range (normalize_small_warp).
-template <int D>
+template <int D, bool FP64_SQUARES = false>
 __device__ __forceinline__ int normalize_small_f64_int(const double* x, double* y, double& r, double& h,
-                                                       bool quat_zero, const SmallKeysF64<D>& kk,
-                                                       bool fp64_squares = false) {
+                                                       bool quat_zero, const SmallKeysF64<D>& kk) {
   if (kk.code == CODE_ZERO) {
 #pragma unroll
     for (int d = 0; d < D; ++d) y[d] = 0.0;
@@ -441,8 +440,8 @@ __device__ __forceinline__ int normalize_small_f64_int(const double* x, double* 
     const uint64_t b = static_cast<uint64_t>(__double_as_longlong(x[d]));
     t[d] = (b << 1) == 0 ? b : b + shift;  // c (+-0) = +-0
   }
-  auto square = [fp64_squares](uint64_t a) {
-    if (fp64_squares) {
+  auto square = [](uint64_t a) {
+    if constexpr (FP64_SQUARES) {
       const double v = __longlong_as_double(static_cast<long long>(a));
       return static_cast<uint64_t>(__double_as_longlong(__dmul_rn(v, v)));
     }
@@ -490,8 +489,10 @@ __device__ __forceinline__ int normalize_small_warp(const T* x, T* y, T& r, T& h
     const SmallKeysF64<D> kk(x);
     const bool all_in_range = __all_sync(0xffffffffu, kk.ok || !active);
     if (!active) return CODE_ZERO;
-    if (kk.ok) return normalize_small_f64_int<D>(x, y, r, h, quat_zero, kk, all_in_range);
-    return normalize_small_hw<T, D>(x, y, r, h, quat_zero);
+    if (!kk.ok) return normalize_small_hw<T, D>(x, y, r, h, quat_zero);
+    // warp-uniform: one copy of the steps per choice, no per-square select
+    if (all_in_range) return normalize_small_f64_int<D, true>(x, y, r, h, quat_zero, kk);
+    return normalize_small_f64_int<D, false>(x, y, r, h, quat_zero, kk);
   } else {
     if (!active) return CODE_ZERO;
     return normalize_small<T, D>(x, y, r, h, quat_zero);

@@ -33,12 +33,34 @@ struct RaggedMapping {
   int grid_blocks;    // persistent grid size; 0 = one full wave
 };
 
+// The work lists of a ragged call, by length class: block items, warp items,
+// thread items, and (binary64) the items of groups of 8 and of 16 lanes.
+enum RaggedList { LIST_BLOCK = 0, LIST_WARP = 1, LIST_THREAD = 2, LIST_GROUP8 = 3, LIST_GROUP16 = 4, NLISTS = 5 };
+
+// Words of the scratch header: counts[NLISTS], tickets[NLISTS], status, then
+// padding to 16 words; the lists follow.
+constexpr int SCRATCH_HEADER_WORDS = 16;
+
 struct RaggedScratch {
-  int32_t* items;    // [3 * count]: block, warp and thread lists back to back
-  int32_t* counts;   // [3] items per list (filled by the classifier)
-  int32_t* tickets;  // [3] work counters of the persistent kernel
+  int32_t* items;    // list k at items[k * count], for the lists the dtype uses
+  int32_t* counts;   // [NLISTS] items per list (filled by the classifier)
+  int32_t* tickets;  // [NLISTS] work counters of the persistent kernel; adjacent to counts
   int32_t* status;   // bit 0: a vector with bad offsets was skipped
 };
+
+// Lists a dtype uses: binary32 has no group lists (the first three lists),
+// binary64 all five.
+constexpr int ragged_lists(int dtype_bytes) { return dtype_bytes == 8 ? NLISTS : 3; }
+
+// RaggedScratch over a buffer of SCRATCH_HEADER_WORDS + lists * count words.
+inline RaggedScratch ragged_scratch(int32_t* buf) {
+  RaggedScratch sc;
+  sc.counts = buf;
+  sc.tickets = buf + NLISTS;
+  sc.status = buf + 2 * NLISTS;
+  sc.items = buf + SCRATCH_HEADER_WORDS;
+  return sc;
+}
 
 template <typename T>
 cudaError_t launch_ragged(const T* x, T* y, T* norm, T* saved_h, int8_t* saved_code, const T* g_or_null,

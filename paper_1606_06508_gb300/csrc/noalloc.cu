@@ -12,9 +12,11 @@
 
 namespace {
 
-// 8 counters/status words followed by three lists of NGB_NOALLOC_MAX_COUNT
-// vector indices: (8 + 3 * 262144) * 4 bytes, about 3 MiB.
-constexpr int64_t kScratchWords = 8 + 3 * (int64_t)NGB_NOALLOC_MAX_COUNT;
+// The counters and status words (ngb::SCRATCH_HEADER_WORDS) followed by the
+// three binary32 work lists of NGB_NOALLOC_MAX_COUNT vector indices:
+// (16 + 3 * 262144) * 4 bytes, about 3 MiB.
+constexpr int64_t kScratchWords =
+    ngb::SCRATCH_HEADER_WORDS + ngb::ragged_lists(4) * (int64_t)NGB_NOALLOC_MAX_COUNT;
 __device__ __align__(256) int32_t g_noalloc_scratch[kScratchWords];
 
 constexpr int kMaxDevices = 64;
@@ -53,13 +55,9 @@ extern "C" ngb_status normalize_ragged_f32_noalloc(const float* x, float* y, flo
   cudaError_t e = scratch_for_current_device(&base);
   if (e != cudaSuccess)
     return ngb::set_last_error(std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e)), NGB_ERR_CUDA;
-  // Same layout as a plan: counts[3], tickets[3], status, pad, then the lists.
-  // launch_ragged clears the counts and tickets on the stream before use.
-  ngb::RaggedScratch sc;
-  sc.counts = base;
-  sc.tickets = base + 3;
-  sc.status = base + 6;
-  sc.items = base + 8;
+  // Same layout as a plan's buffer (ngb::ragged_scratch); launch_ragged
+  // clears the counts and tickets on the stream before use.
+  const ngb::RaggedScratch sc = ngb::ragged_scratch(base);
   ngb::RaggedMapping map{8, 8192, 256, 0};
   map.grid_blocks = ngb::ragged_full_wave<float>(map, false);
   e = ngb::launch_ragged<float>(x, y, norm, saved_h, saved_code, nullptr, nullptr, nullptr, nullptr, offsets, count,

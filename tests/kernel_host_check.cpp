@@ -55,7 +55,7 @@ static int fwd_small(const T* x, T* y, T& r, T& h, bool qz, const char* mode) {
   if (!strcmp(mode, "sq64")) {
     if constexpr (sizeof(T) == 8) {
       const SmallKeysF64<D> kk(x);
-      if (kk.ok) return normalize_small_f64_int<D>(x, y, r, h, qz, kk, true);
+      if (kk.ok) return normalize_small_f64_int<D, true>(x, y, r, h, qz, kk);
       return normalize_small_hw<T, D>(x, y, r, h, qz);
     }
     fprintf(stderr, "sq64 is a binary64 mode\n");

@@ -14,15 +14,20 @@
 //   batch   one warp streaming 4 rows with one square root and reciprocal
 //           (warp_forward_stream_batch)
 //   block   one block of 256 threads streaming the row (block_forward_stream)
+//   group8, group16  groups of W = 8 or 16 lanes, 32 / W rows per warp
+//           (csrc/ngb_grouppath.cuh), n <= 8 W; row i holds a vector of
+//           length n - (i mod 5) (at least 5) in its first components, so
+//           that the groups of a warp differ in length
 // Backward paths read y, g (count x n each), h (count) and code (count bytes)
-// and write grad (count x n): warp_bwd (n <= 1024), stream_bwd, block_bwd.
+// and write grad (count x n): warp_bwd (n <= 1024), stream_bwd, block_bwd,
+// group8_bwd, group16_bwd (lengths as the group forward paths).
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
 
-#include "ngb_rowpath.cuh"
+#include "ngb_grouppath.cuh"
 
 using namespace ngb;
 
@@ -87,6 +92,32 @@ static void warp_dispatch(Rows<T>& d) {
   }
 }
 
+// Row lengths of the group paths.
+static int group_len(int n, int64_t row) {
+  const int m = n - (int)(row % 5);
+  return m < 5 ? 5 : m;
+}
+
+template <typename T, int W, bool BWD>
+static void group_rows(Rows<T>& d) {
+  constexpr int PER = 32 / W;
+  hemu::run_block(64, [&] {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = threadIdx.x >> 5, nw = 2;
+    VecOut<T> out{d.r.data(), d.h.data(), d.code.data()};
+    for (int64_t r0 = w0 * PER; r0 < d.count; r0 += nw * PER) {
+      const int64_t row = r0 + lane / W;
+      if (row >= d.count) continue;
+      const int len = group_len(d.n, row);
+      if (BWD)
+        group_backward<T, W>(d.y.data() + row * d.n, d.g.data() + row * d.n, d.grad.data() + row * d.n, len, lane,
+                             d.h[row], d.code[row]);
+      else
+        group_forward<T, W>(d.x.data() + row * d.n, d.y.data() + row * d.n, len, lane, out, row);
+    }
+  });
+}
+
 template <typename T>
 static void run_path(Rows<T>& d, const std::string& path) {
   VecOut<T> out{d.r.data(), d.h.data(), d.code.data()};
@@ -110,6 +141,15 @@ static void run_path(Rows<T>& d, const std::string& path) {
         }
       });
     }
+  } else if (path == "group8" || path == "group16" || path == "group8_bwd" || path == "group16_bwd") {
+    const bool bwd = path.size() > 4 && path.compare(path.size() - 4, 4, "_bwd") == 0;
+    const int W = path.compare(0, 7, "group16") == 0 ? 16 : 8;
+    if (n > 8 * W) {
+      fprintf(stderr, "group paths take n <= 8 W\n");
+      exit(2);
+    }
+    if (W == 8) bwd ? group_rows<T, 8, true>(d) : group_rows<T, 8, false>(d);
+    else bwd ? group_rows<T, 16, true>(d) : group_rows<T, 16, false>(d);
   } else if (path == "stream") {
     hemu::run_block(64, [&] {
       const int lane = threadIdx.x & 31;

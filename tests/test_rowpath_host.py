@@ -126,3 +126,64 @@ def test_rows_backward_matches_oracle(rph, f, n, path):
 def test_f64_backward_integer_pipe_limits(rph, n, path):
     x = f64_range_edges(12, n, seed=2 * n)
     _backward(rph, "f64", n, path, x, f"f64 limits n={n} {path}")
+
+
+def _group_lengths(cnt, n):
+    return np.maximum(5, n - np.arange(cnt) % 5)
+
+
+def _pack(rows2d, lengths):
+    return np.concatenate([rows2d[i, :m] for i, m in enumerate(lengths)])
+
+
+@pytest.mark.parametrize("f,n,w,cnt", [("f64", 64, 8, 37), ("f64", 9, 8, 21), ("f64", 128, 16, 23),
+                                       ("f64", 65, 16, 19), ("f32", 64, 8, 29), ("f32", 128, 16, 19)])
+def test_group_forward_and_backward_match_oracle(rph, f, n, w, cnt):
+    """Groups of 8 or 16 lanes (csrc/ngb_grouppath.cuh), one vector each, the
+    groups of a warp on vectors of different lengths and kinds (zero, NaN,
+    infinite, subnormal components; scaled and unscaled), forward and
+    backward; binary64 also at the limits of the integer-pipe steps."""
+    dt = DT[f]
+    sets = [_rows(f, cnt, n, seed=7 * n + w)]
+    if f == "f64":
+        sets.append(f64_range_edges(cnt, n, seed=n + w))
+    for k, x in enumerate(sets):
+        lengths = _group_lengths(x.shape[0], n)
+        for i, m in enumerate(lengths):
+            x[i, m:] = 0  # components past the vector's length are not part of it
+        off = synth.offsets_from_lengths(lengths)
+        xp = _pack(x, lengths)
+        oy, orr, oh, oc = oracle.normalize(xp, dim=0, offsets=off)
+        raw = _call(rph, f, n, f"group{w}", [x.reshape(-1)])
+        c_ = x.shape[0]
+        s_ = dt(0).itemsize
+        y = raw[: c_ * n * s_].view(dt).reshape(c_, n)
+        what = f"{f} n<={n} group{w} set {k}"
+        assert_bits(_pack(y, lengths), oy, what + " y")
+        assert_bits(raw[c_ * n * s_: (c_ * n + c_) * s_].view(dt), orr, what + " norm")
+        assert_bits(raw[(c_ * n + c_) * s_: (c_ * n + 2 * c_) * s_].view(dt), oh, what + " h")
+        assert_bits(raw[(c_ * n + 2 * c_) * s_:].view(np.int8), oc, what + " code")
+        g = np.random.default_rng(n + k).standard_normal((c_, n)).astype(dt)
+        yr = np.zeros((c_, n), dt)
+        for i, m in enumerate(lengths):
+            yr[i, :m] = oy[off[i]:off[i + 1]]
+            g[i, m:] = 0
+        og = oracle.backward(oy, _pack(g, lengths), oh, oc, dim=0, offsets=off)
+        rawb = _call(rph, f, n, f"group{w}_bwd", [yr, g, oh, oc.astype(np.int8)])
+        assert_bits(_pack(rawb.view(dt).reshape(c_, n), lengths), og, what + " grad")
+
+
+@pytest.mark.parametrize("n", [1025, 5000])
+def test_stream_speculation_falls_back(rph, n):
+    """binary32 streaming rows whose first 256 components select another
+    factor than the whole row (a larger component later): the speculative sum
+    is dropped and the second pass gives the oracle's bits."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal((6, n)).astype(np.float32)
+    x[0, 700] = 2.0 ** 60          # first round: c = 1; row: sigma_max
+    x[1, :256] *= 2.0 ** -80       # first round: sigma_min; row: c = 1
+    x[2, :] *= 2.0 ** -80
+    x[2, n - 1] = 2.0 ** 70        # first round: sigma_min; row: sigma_max
+    x[3, :] *= 2.0 ** 60           # the whole row sigma_max (speculation holds)
+    x[4, :256] = 0                 # first round all zero; row: c = 1
+    _forward(rph, "f32", n, "stream", x, f"f32 n={n} speculation")
