@@ -4,8 +4,9 @@
 //
 //   dim <= 4           one vector per thread (Algorithms 5-7); 16-byte vector
 //                      loads when a vector is 16 bytes (binary32 quaternions,
-//                      binary64 pairs), otherwise a 256-vector tile staged
-//                      through shared memory with 16-byte loads.
+//                      binary64 pairs) or two of them (binary64 quaternions),
+//                      otherwise one load per component (a warp's loads cover
+//                      consecutive lines; L1 serves the repeats).
 //   5 <= dim <= 16     one vector per thread, order CR(n).
 //   17 <= dim <= 1024  one warp per row held in registers, 16-byte loads when
 //                      rows are 16-byte aligned.
@@ -100,9 +101,14 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_vec16(const T* __restri
 // binary64 takes one vector at a time: its integer-pipe steps are long, and
 // fewer registers give more warps (measured on 2^25 quaternions: U = 4
 // 1.34 ms, 2 1.18 ms, 1 1.18 ms, 8 1.55 ms).
+// pairs (binary64, D = 4, x and y 16-byte aligned): each quaternion is read
+// and written as two 16-byte pairs instead of four scalars.  On device memory
+// L1 serves the repeated lines of the scalar form either way; on pinned host
+// memory (zero-copy) the scalar form fetched each line again over the host
+// link and ran 2.2 times slower than staging the copies.
 template <typename T, int D>
 __global__ void __launch_bounds__(SMALL_THREADS) k_small_direct(const T* __restrict__ x, T* y, VecOut<T> out,
-                                                                 int64_t count, int quat_zero) {
+                                                                 int64_t count, int quat_zero, int pairs) {
   constexpr int U = sizeof(T) == 8 ? 1 : 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if constexpr (sizeof(T) == 4) {
@@ -138,6 +144,18 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_direct(const T* __restr
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int64_t i = i0 + u * stride;
+        if constexpr (D == 4) {
+          if (pairs) {  // uniform over the launch
+            if (i < count) {
+              Vec<T, 2>::load(x + i * D, xv[u]);
+              Vec<T, 2>::load(x + i * D + 2, xv[u] + 2);
+            } else {
+#pragma unroll
+              for (int k = 0; k < D; ++k) xv[u][k] = T(0);
+            }
+            continue;
+          }
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) xv[u][k] = i < count ? __ldcs(x + i * D + k) : T(0);
       }
@@ -149,8 +167,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_direct(const T* __restr
           const int code = normalize_small_warp<T, D>(xv[u], yv, r, h, quat_zero != 0, i < count);
           if (i < count) {
             if (y) {
+              if (D == 4 && pairs) {
+                Vec<T, 2>::store(y + i * D, yv);
+                Vec<T, 2>::store(y + i * D + 2, yv + 2);
+              } else {
 #pragma unroll
-              for (int k = 0; k < D; ++k) __stcs(y + i * D + k, yv[k]);
+                for (int k = 0; k < D; ++k) __stcs(y + i * D + k, yv[k]);
+              }
             }
             out.put(i, r, h, code);
           }
@@ -371,7 +394,8 @@ cudaError_t launch_small_fwd(const T* x, T* y, VecOut<T> out, int64_t count, boo
   {
     auto k = k_small_direct<T, D>;
     const int grid = grid_for(k, SMALL_THREADS, count, SMALL_THREADS);  // small batches: one vector per thread
-    k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero);
+    const int pairs = (sizeof(T) == 8 && D == 4 && vec16) ? 1 : 0;
+    k<<<grid, SMALL_THREADS, 0, s>>>(x, y, out, count, quat_zero, pairs);
   }
   return cudaGetLastError();
 }
