@@ -218,6 +218,23 @@ ngb_status quotient_normalize3_f64(const double* x, double* y, double* norm, int
  * null out or non-positive sizes, NGB_ERR_CUDA for a launch failure. */
 ngb_status ngb_fp64_probe(double* out, int32_t blocks, int32_t iters, int64_t* fp64_ops, ngb_stream_t stream);
 
+/*
+ * ngb_shard_range -- one process per GPU, every vector independent: the
+ * contiguous vectors [*begin, *end) that rank `rank` of `world` normalizes,
+ * with no data exchanged between ranks.  Dense batch (offsets == NULL):
+ * split by vector count, begin = floor(count rank / world).  Ragged batch:
+ * offsets is a HOST int64[count + 1] array (nondecreasing); the split
+ * balances the element count: rank r starts at the first vector whose start
+ * offset is at least offsets[0] + floor(total r / world), total =
+ * offsets[count] - offsets[0], so each shard's element count is within one
+ * vector's length of total / world.  The ranges of ranks 0 .. world-1 are
+ * disjoint and cover [0, count).  Host-only; no CUDA call.  Errors:
+ * NGB_ERR_INVALID_ARG for a NULL begin or end, count < 0, world < 1 or rank
+ * outside [0, world).
+ */
+ngb_status ngb_shard_range(const int64_t* offsets, int64_t count, int32_t world, int32_t rank, int64_t* begin,
+                           int64_t* end);
+
 /* Largest batch accepted by normalize_ragged_f32_noalloc. */
 #define NGB_NOALLOC_MAX_COUNT 262144
 

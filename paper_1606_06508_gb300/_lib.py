@@ -57,6 +57,7 @@ PROTOTYPES = {
     "quotient_normalize3_f64": (ST, [P, P, P, I64, I32, P]),
     "naive_normalize_f32": (ST, [P, P, I64, I32, P]),
     "naive_normalize_f64": (ST, [P, P, I64, I32, P]),
+    "ngb_shard_range": (ST, [P, I64, I32, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
     "normalize_ragged_f32_noalloc": (ST, [P, P, P, P, P, I64, P, U32, P]),
     "ngb_last_error": (ctypes.c_char_p, []),
     "ngb_version": (ctypes.c_char_p, []),
@@ -137,6 +138,13 @@ def ngb_plan_create(count: int, dtype_bytes: int, capacity: int = 0):
     h = P()
     st = lib().ngb_plan_create(ctypes.byref(h), count, dtype_bytes, capacity)
     return st, h.value
+
+
+def ngb_shard_range(offsets_ptr, count: int, world: int, rank: int):
+    """Returns (status, begin, end); offsets_ptr is a host address or None."""
+    b, e = I64(), I64()
+    st = lib().ngb_shard_range(offsets_ptr, count, world, rank, ctypes.byref(b), ctypes.byref(e))
+    return st, b.value, e.value
 
 
 def ngb_plan_get_mapping(plan):

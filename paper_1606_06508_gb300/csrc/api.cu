@@ -471,6 +471,31 @@ ngb_status naive_normalize_f64(const double* x, double* y, int64_t count, int32_
   return e == cudaSuccess ? NGB_OK : cuda_fail(e, "naive launch");
 }
 
+ngb_status ngb_shard_range(const int64_t* offsets, int64_t count, int32_t world, int32_t rank, int64_t* begin,
+                           int64_t* end) {
+  g_last_error.clear();
+  if (!begin || !end) return fail(NGB_ERR_INVALID_ARG, "begin and end are required");
+  if (count < 0 || world < 1 || rank < 0 || rank >= world)
+    return fail(NGB_ERR_INVALID_ARG, "need count >= 0, world >= 1 and 0 <= rank < world");
+  // floor(a r / world) without overflow for any int64 a >= 0 and r <= world
+  auto part = [world](int64_t a, int64_t r) { return (int64_t)(((__int128)a * r) / world); };
+  if (!offsets) {
+    *begin = part(count, rank);
+    *end = part(count, (int64_t)rank + 1);
+    return NGB_OK;
+  }
+  const int64_t total = offsets[count] - offsets[0];
+  auto cut = [&](int64_t r) -> int64_t {
+    if (r <= 0) return 0;
+    if (r >= world) return count;
+    const int64_t target = offsets[0] + part(total, r);
+    return (int64_t)(std::lower_bound(offsets, offsets + count, target) - offsets);  // first start >= target
+  };
+  *begin = cut(rank);
+  *end = cut((int64_t)rank + 1);
+  return NGB_OK;
+}
+
 const char* ngb_last_error(void) { return g_last_error.c_str(); }
 
 const char* ngb_version(void) { return "normgb 0.1.0 (sm_103a)"; }

@@ -549,8 +549,10 @@ __device__ __forceinline__ void block_backward_stream(const T* __restrict__ yr, 
 }
 
 // ---------------------------------------------------------------------------
-// Rounds of 8 loads per lane that a binary32 streaming pass keeps in flight.
-constexpr int STREAM_ROUNDS = 2;
+// Rounds of 8 loads per lane that a binary32 streaming pass keeps in flight
+// (ragged binary32 workload, fraction of the copy bandwidth: 2 rounds 0.870,
+// 3 rounds 0.877 at the same 48 registers; 4 and 8 spill and run slower).
+constexpr int STREAM_ROUNDS = 3;
 
 // Streaming warp layout (any length).  Lane l reads the elements
 // k = 32 c + l, c = 0, 1, ..., eight chunks (256 elements) per round; slot

@@ -134,6 +134,49 @@ def test_shard_ranges_partition():
         assert max(elems) - min(elems) <= 2 * 4096 + off[-1] // 100
 
 
+def test_shard_range_matches_its_definition(lib):
+    """ngb_shard_range against the definition written out: dense, the floor of
+    count * rank / world; ragged, the first vector whose start is at least
+    offsets[0] + floor(total * rank / world) (offsets not starting at 0, empty
+    vectors included); argument errors."""
+    import numpy as np
+    L = lib
+    rng = np.random.default_rng(5)
+    for count in (0, 1, 2, 7, 1000, 2 ** 40):
+        for world in (1, 2, 3, 8, 13):
+            for rank in range(world):
+                st, a, b = L.ngb_shard_range(None, count, world, rank)
+                assert st == L.NGB_OK and (a, b) == (count * rank // world, count * (rank + 1) // world)
+    for trial in range(30):
+        count = int(rng.integers(0, 300))
+        lengths = rng.integers(0, 50, size=count)
+        lengths[rng.random(count) < 0.2] = 0
+        start = int(rng.integers(0, 100))
+        off = (start + np.concatenate([[0], np.cumsum(lengths)])).astype(np.int64)
+        total = int(off[-1] - off[0])
+        for world in (1, 2, 5, 8):
+            bounds = []
+            for rank in range(world):
+                st, a, b = L.ngb_shard_range(off.ctypes.data, count, world, rank)
+                assert st == L.NGB_OK
+                def cut(r):
+                    if r <= 0:
+                        return 0
+                    if r >= world:
+                        return count
+                    target = int(off[0]) + total * r // world
+                    return next((i for i in range(count) if off[i] >= target), count)
+                assert (a, b) == (cut(rank), cut(rank + 1)), (trial, world, rank)
+                bounds.append((a, b))
+            assert bounds[0][0] == 0 and bounds[-1][1] == count
+            assert all(bounds[i][1] == bounds[i + 1][0] for i in range(world - 1))
+            if count:
+                assert all(abs(int(off[b] - off[a]) - total / world) <= int(lengths.max()) for a, b in bounds)
+    assert L.ngb_shard_range(None, 5, 0, 0)[0] == L.NGB_ERR_INVALID_ARG
+    assert L.ngb_shard_range(None, 5, 2, 2)[0] == L.NGB_ERR_INVALID_ARG
+    assert L.ngb_shard_range(None, -1, 2, 0)[0] == L.NGB_ERR_INVALID_ARG
+
+
 def _gloo_worker(rank, world, port, q):
     import torch
     import torch.distributed as dist
