@@ -76,17 +76,22 @@ template cudaError_t launch_rotation<double>(const double*, double*, double*, in
 // ---------------------------------------------------------------------------
 // Measurement aid: a streaming copy with 16-byte loads and stores, the
 // achievable bandwidth ceiling for the same bytes.
+// Warp tiles of 32 U consecutive 16-byte words over a covering grid, the
+// layout of the quaternion kernel (k_small_vec16), so that the ceiling is
+// taken with the same access pattern.
+constexpr int COPY16_IN_FLIGHT = 6;
 __global__ void __launch_bounds__(256) k_copy16(const uint4* __restrict__ src, uint4* __restrict__ dst, int64_t n16) {
-  constexpr int U = 4;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < n16; i0 += stride * U) {
+  constexpr int U = COPY16_IN_FLIGHT;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32 * U; w0 < n16; w0 += nw * 32 * U) {
     uint4 v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (i0 + u * stride < n16) v[u] = __ldcs(src + i0 + u * stride);
+      if (w0 + 32 * u + lane < n16) v[u] = __ldcs(src + w0 + 32 * u + lane);
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (i0 + u * stride < n16) __stcs(dst + i0 + u * stride, v[u]);
+      if (w0 + 32 * u + lane < n16) __stcs(dst + w0 + 32 * u + lane, v[u]);
   }
 }
 
@@ -98,14 +103,11 @@ __global__ void k_copy1(const unsigned char* __restrict__ src, unsigned char* __
 cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t s) {
   const bool al = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15u) == 0 &&
                   (bytes % 16) == 0;
-  int per_sm = 0;
   if (al) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_copy16, 256, 0);
     const int64_t n16 = bytes / 16;
-    int64_t need = (n16 + 1023) / 1024;
-    int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
-    k_copy16<<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(
-        reinterpret_cast<const uint4*>(src), reinterpret_cast<uint4*>(dst), n16);
+    int64_t need = (n16 + 256 * COPY16_IN_FLIGHT - 1) / (256 * COPY16_IN_FLIGHT);
+    need = need < 1 ? 1 : (need < 2147483647 ? need : 2147483647);
+    k_copy16<<<(int)need, 256, 0, s>>>(reinterpret_cast<const uint4*>(src), reinterpret_cast<uint4*>(dst), n16);
   } else {
     k_copy1<<<device_sm_count() * 8, 256, 0, s>>>(reinterpret_cast<const unsigned char*>(src),
                                                   reinterpret_cast<unsigned char*>(dst), bytes);
@@ -113,19 +115,24 @@ cudaError_t launch_copy(void* dst, const void* src, int64_t bytes, cudaStream_t 
   return cudaGetLastError();
 }
 
+// The naive kernel's layout is that of the scaling kernels it is compared
+// with (warp tiles of 32 U vectors, a covering grid, 6 vectors in flight).
+constexpr int NAIVE_IN_FLIGHT = 6;
+
 // Measurement aid: the naive algorithm the paper compares with in Table 4,
 // y = x * (1 / sqrt(x1^2 + ... + xd^2)) with no scaling (it overflows and
 // underflows where the scaling algorithms do not), for d <= 4.
 template <typename T, int D>
 __global__ void __launch_bounds__(256) k_naive(const T* __restrict__ x, T* __restrict__ y, int64_t count, int vec) {
   using F = FP<T>;
-  constexpr int U = 4;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < count; i0 += stride * U) {
+  constexpr int U = NAIVE_IN_FLIGHT;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32 * U; w0 < count; w0 += nw * 32 * U) {
     T v[U][D];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
+      const int64_t i = w0 + 32 * u + lane;
       if (i < count) {
         if constexpr (D * sizeof(T) == 16) {
           if (vec) { Vec<T, D>::load(x + i * D, v[u]); continue; }
@@ -136,7 +143,7 @@ __global__ void __launch_bounds__(256) k_naive(const T* __restrict__ x, T* __res
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + u * stride;
+      const int64_t i = w0 + 32 * u + lane;
       if (i < count) {
         T s = F::mul(v[u][0], v[u][0]);
 #pragma unroll
@@ -158,11 +165,9 @@ __global__ void __launch_bounds__(256) k_naive(const T* __restrict__ x, T* __res
 template <typename T, int D>
 static cudaError_t launch_naive_d(const T* x, T* y, int64_t count, cudaStream_t s) {
   const int vec = (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15u) == 0) ? 1 : 0;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_naive<T, D>, 256, 0);
-  int64_t need = (count + 1023) / 1024;
-  int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
-  k_naive<T, D><<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(x, y, count, vec);
+  int64_t need = (count + 256 * NAIVE_IN_FLIGHT - 1) / (256 * NAIVE_IN_FLIGHT);
+  need = need < 1 ? 1 : (need < 2147483647 ? need : 2147483647);
+  k_naive<T, D><<<(int)need, 256, 0, s>>>(x, y, count, vec);
   return cudaGetLastError();
 }
 
