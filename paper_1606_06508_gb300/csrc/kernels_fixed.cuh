@@ -93,8 +93,9 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_small_vec16(const T* __restri
 // binary64 takes one vector at a time: its integer-pipe steps are long, and
 // fewer registers give more warps (measured on 2^25 quaternions: U = 4
 // 1.34 ms, 2 1.18 ms, 1 1.18 ms, 8 1.55 ms; with the FP64 squares, U = 2
-// 0.882 ms against 0.871 ms).
-template <typename T> constexpr int SMALL_DIRECT_IN_FLIGHT = sizeof(T) == 8 ? 1 : 4;
+// 0.882 ms against 0.871 ms).  binary32 (2^24 three-component vectors, warp
+// tiles): U = 2 0.088 ms, 4 0.0724 ms, 6 0.0716 ms, 8 0.080 ms.
+template <typename T> constexpr int SMALL_DIRECT_IN_FLIGHT = sizeof(T) == 8 ? 1 : 6;
 // pairs (binary64, D = 4, x and y 16-byte aligned): each quaternion is read
 // and written as two 16-byte pairs instead of four scalars.  On device memory
 // L1 serves the repeated lines of the scalar form either way; on pinned host
