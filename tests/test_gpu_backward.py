@@ -30,7 +30,7 @@ def _np(t):
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])
-@pytest.mark.parametrize("dim", [1, 2, 3, 4, 5, 9, 16, 17, 33, 64, 65, 129, 256, 257, 1000, 1023, 1500, 2500,
+@pytest.mark.parametrize("dim", [1, 2, 3, 4, 5, 9, 16, 17, 33, 64, 65, 100, 128, 129, 256, 257, 1000, 1023, 1500, 2500,
                                  4096, 5000])
 def test_dense_backward(dev, f, dim):
     from paper_1606_06508_gb300 import api

@@ -119,7 +119,7 @@ def test_misaligned_and_inplace(dev, f, dim):
 
 
 @pytest.mark.parametrize("f", ["f32", "f64"])
-@pytest.mark.parametrize("dim", [5, 7, 16, 17, 31, 32, 33, 64, 100, 132, 200, 252, 255, 256, 257, 512, 1000, 1024, 1025, 2048,
+@pytest.mark.parametrize("dim", [5, 7, 16, 17, 31, 32, 33, 64, 65, 100, 127, 128, 129, 132, 200, 252, 255, 256, 257, 512, 1000, 1024, 1025, 2048,
                                  3000, 4096, 4097, 20000])
 def test_rows(dev, f, dim):
     dt = DT[f]
@@ -196,9 +196,10 @@ def test_small_f64_integer_pipe_limits(dev, dim):
 @pytest.mark.parametrize("f", ["f32", "f64"])
 @pytest.mark.parametrize("count", [1, 2, 3, 1001])
 def test_rows_odd_counts(dev, f, count):
-    """Row kernels that put two rows on one warp: odd counts leave the last
-    warp's second half without a row of its own."""
+    """Row kernels that put several rows on one warp (half-warps, groups of 8
+    or 16 lanes): counts that are not a multiple leave the last warp's later
+    groups without a row of their own."""
     dt = DT[f]
-    for dim in (132, 256):
+    for dim in (20, 64, 100, 132, 256):
         x = synth.rows(count, dim, dt, seed=count + dim)
         _check_forward(dev, x, dim, what=f"{f} rows d={dim} count={count}")
