@@ -63,11 +63,10 @@ __global__ void __launch_bounds__(256) k_rotation(const T* __restrict__ q, T* __
 
 template <typename T>
 cudaError_t launch_rotation(const T* q, T* R, T* norm, int64_t count, cudaStream_t s) {
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rotation<T>, 256, 0);
+  // a grid that covers the batch (one quaternion per thread), as the dense normalization kernels
   int64_t need = (count + 255) / 256;
-  int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
-  k_rotation<T><<<(int)(need < cap ? (need > 0 ? need : 1) : cap), 256, 0, s>>>(q, R, norm, count);
+  need = need < 1 ? 1 : (need < 2147483647 ? need : 2147483647);
+  k_rotation<T><<<(int)need, 256, 0, s>>>(q, R, norm, count);
   return cudaGetLastError();
 }
 template cudaError_t launch_rotation<float>(const float*, float*, float*, int64_t, cudaStream_t);
@@ -244,12 +243,11 @@ __global__ void __launch_bounds__(256) k_quotient3(const T* __restrict__ x, T* y
 
 template <typename T>
 cudaError_t launch_quotient3(const T* x, T* y, T* norm, int64_t count, int alg, cudaStream_t s) {
-  int per_sm = 0;
-  if (alg == 1) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quotient3<T, 1>, 256, 0);
-  else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quotient3<T, 2>, 256, 0);
-  const int64_t need = (count + 255) / 256;
-  const int64_t cap = (int64_t)(per_sm > 0 ? per_sm : 1) * device_sm_count();
-  const int grid = (int)(need < cap ? (need > 0 ? need : 1) : cap);
+  // a grid that covers the batch (one tile of 256 vectors per block), the launch shape of the
+  // scaling kernels it is compared with (Table 3)
+  int64_t need = (count + 255) / 256;
+  need = need < 1 ? 1 : (need < 2147483647 ? need : 2147483647);
+  const int grid = (int)need;
   if (alg == 1) k_quotient3<T, 1><<<grid, 256, 0, s>>>(x, y, norm, count);
   else k_quotient3<T, 2><<<grid, 256, 0, s>>>(x, y, norm, count);
   return cudaGetLastError();
