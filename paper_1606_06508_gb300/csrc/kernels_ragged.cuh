@@ -272,13 +272,31 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
     if (lane == 0) base = atomicAdd(&a.sc.tickets[LIST_WARP], WARP_BATCH);
     base = __shfl_sync(FULL, base, 0);
     if (base >= nwarp) break;
-    for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
-      const int64_t vec = Lw[base + j];
-      const int64_t s = a.off[vec];
-      const int n = (int)(a.off[vec + 1] - s);
-      if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
-        prefetch_item_l2(a, Lw[base + j + 1], lane);
-      warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+    if constexpr (sizeof(T) == 8) {
+      // binary64: two items at a time share one square root and reciprocal
+      // (warp_forward_stream_batch; the pair's vectors stay in L1 between
+      // passes 2 and 3).  Measured: forward 7.34 -> 7.29 ms, forward +
+      // backward 1.67 -> 1.645 ms; four at a time 7.34 and 1.63 ms.
+      for (int j = 0; j < WARP_BATCH && base + j < nwarp; j += 2) {
+        const int nb = (nwarp - (base + j)) < 2 ? (nwarp - (base + j)) : 2;
+        auto item = [&](int jj, const T*& xr, T*& yr, int& nn, int64_t& vec) {
+          vec = Lw[base + j + jj];
+          const int64_t s = a.off[vec];
+          nn = (int)(a.off[vec + 1] - s);
+          xr = a.x + s;
+          yr = a.y ? a.y + s : nullptr;
+        };
+        warp_forward_stream_batch<T, 2, MAX_LEN, true>(item, nb, lane, a.out);
+      }
+    } else {
+      for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
+        const int64_t vec = Lw[base + j];
+        const int64_t s = a.off[vec];
+        const int n = (int)(a.off[vec + 1] - s);
+        if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
+          prefetch_item_l2(a, Lw[base + j + 1], lane);
+        warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+      }
     }
   }
 

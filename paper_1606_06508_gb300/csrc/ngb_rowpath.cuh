@@ -885,7 +885,9 @@ __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T*
 // done one by one on the spot: between passes 2 and 3 the batch's vectors
 // must stay in L1.  The loops over the batch are not unrolled: one copy of
 // each pass keeps the kernel small.
-template <typename T, int NB, int MAX_N, typename Item>
+// TAIL_SKIP as in stream_pass2_any: true for ragged vectors (partial last
+// rounds), false for dense rows.
+template <typename T, int NB, int MAX_N, bool TAIL_SKIP = false, typename Item>
 __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int nb, int lane, const VecOut<T>& out) {
   T s = T(1);
   int code_l = CODE_ONE;  // lane j < nb: the code of vector j
@@ -910,7 +912,7 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
         code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, sj, have_s);
       }
       if (code != CODE_ZERO) {
-        if (!have_s) sj = stream_pass2_any<T, false>(xr, n, lane, code, emu);
+        if (!have_s) sj = stream_pass2_any<T, TAIL_SKIP>(xr, n, lane, code, emu);
         if (lane == j) {
           s = sj;
           code_l = code;

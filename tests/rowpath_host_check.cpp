@@ -14,6 +14,10 @@
 //   batch   one warp streaming 4 rows with one square root and reciprocal
 //           (warp_forward_stream_batch)
 //   block   one block of 256 threads streaming the row (block_forward_stream)
+//   pairs   one warp streaming 2 rows of different lengths with one square
+//           root and reciprocal and the partial-round skip (the ragged
+//           binary64 warp items: warp_forward_stream_batch<T, 2, MAX_LEN, true>);
+//           row i holds a vector of length n - (i mod 5) (at least 5)
 //   group8, group16  groups of W = 8 or 16 lanes, 32 / W rows per warp
 //           (csrc/ngb_grouppath.cuh), n <= 8 W; row i holds a vector of
 //           length n - (i mod 5) (at least 5) in its first components, so
@@ -141,6 +145,21 @@ static void run_path(Rows<T>& d, const std::string& path) {
         }
       });
     }
+  } else if (path == "pairs") {
+    hemu::run_block(64, [&] {
+      const int lane = threadIdx.x & 31;
+      const int64_t w0 = threadIdx.x >> 5, nw = 2;
+      for (int64_t g = w0 * 2; g < d.count; g += nw * 2) {
+        const int nb = (int)((d.count - g) < 2 ? (d.count - g) : 2);
+        auto item = [&](int j, const T*& xr, T*& yr, int& nn, int64_t& vec) {
+          vec = g + j;
+          xr = d.x.data() + vec * n;
+          yr = d.y.data() + vec * n;
+          nn = group_len(n, vec);
+        };
+        warp_forward_stream_batch<T, 2, MAX_LEN, true>(item, nb, lane, out);
+      }
+    });
   } else if (path == "group8" || path == "group16" || path == "group8_bwd" || path == "group16_bwd") {
     const bool bwd = path.size() > 4 && path.compare(path.size() - 4, 4, "_bwd") == 0;
     const int W = path.compare(0, 7, "group16") == 0 ? 16 : 8;

@@ -187,3 +187,27 @@ def test_stream_speculation_falls_back(rph, n):
     x[3, :] *= 2.0 ** 60           # the whole row sigma_max (speculation holds)
     x[4, :256] = 0                 # first round all zero; row: c = 1
     _forward(rph, "f32", n, "stream", x, f"f32 n={n} speculation")
+
+
+@pytest.mark.parametrize("f,n,cnt", [("f64", 300, 11), ("f64", 1000, 9), ("f64", 40, 13), ("f32", 700, 9)])
+def test_pairs_forward_matches_oracle(rph, f, n, cnt):
+    """Two vectors of different lengths per warp sharing one square root and
+    reciprocal, with the partial-round skip (the ragged binary64 warp items),
+    against the oracle; binary64 also at the integer-pipe limits."""
+    dt = DT[f]
+    sets = [_rows(f, cnt, n, seed=3 * n + cnt)]
+    if f == "f64":
+        sets.append(f64_range_edges(cnt, n, seed=n + 1))
+    for k, x in enumerate(sets):
+        lengths = _group_lengths(x.shape[0], n)
+        for i, m in enumerate(lengths):
+            x[i, m:] = 0
+        off = synth.offsets_from_lengths(lengths)
+        oy, orr, oh, oc = oracle.normalize(_pack(x, lengths), dim=0, offsets=off)
+        raw = _call(rph, f, n, "pairs", [x.reshape(-1)])
+        c_, s_ = x.shape[0], dt(0).itemsize
+        what = f"{f} n<={n} pairs set {k}"
+        assert_bits(_pack(raw[: c_ * n * s_].view(dt).reshape(c_, n), lengths), oy, what + " y")
+        assert_bits(raw[c_ * n * s_: (c_ * n + c_) * s_].view(dt), orr, what + " norm")
+        assert_bits(raw[(c_ * n + c_) * s_: (c_ * n + 2 * c_) * s_].view(dt), oh, what + " h")
+        assert_bits(raw[(c_ * n + 2 * c_) * s_:].view(np.int8), oc, what + " code")
