@@ -16,7 +16,8 @@
 //    items, lanes on thread items.  Warps and blocks stream their vector
 //    (three passes, a few partial sums per lane) instead of holding it, so
 //    the kernel keeps few registers and many loads in flight; in binary32 a
-//    warp prefetches its next item into L2 while it works on the current one.
+//    warp prefetches its next item into L2 once pass 1 has read the current
+//    one.
 //    Groups hold their (short) vector in registers.  No block ever waits for
 //    another.
 // 3. Backward: one plain grid-stride kernel per list (k_ragged_bwd_blocks,
@@ -31,7 +32,8 @@
 namespace ngb {
 
 constexpr int CLASSIFY_THREADS = 1024;
-constexpr int WARP_BATCH = 4;     // warp items per ticket (binary32 ragged: 4 0.847, 8 0.843, 16 0.825)
+constexpr int WARP_BATCH = 8;     // warp items per ticket (binary32 ragged, prefetch after pass 1: 4 1.941 ms, 8 1.933 ms;
+                                  // binary64 ragged: 4 7.293 ms, 8 7.288 ms)
 constexpr int THREAD_BATCH = 4;   // 32-item groups per ticket
 constexpr int GROUP_BATCH = 4;    // rounds of 32 / W group items per ticket
 
@@ -189,11 +191,17 @@ struct RaggedArgs {
 // Forward persistent kernel, B threads per block (128 or 256).  Resident
 // threads per SM requested: 5 x 256 for binary32 (at most 48 registers),
 // 3 x 256 for binary64 (at most 80, no spills).
-// L2 prefetch of the next warp item's vector (within the ticket) while the
-// current item runs.  Measured on the ragged workloads: binary32 0.798 ->
-// 0.846 of the copy bandwidth (a whole ticket at once: 0.829; the next
-// ticket taken one ahead to prefetch across tickets: 0.827); binary64, bound
-// by the FP64 pipe, 0.401 -> 0.388: off.
+// L2 prefetch of the next warp item's vector (within the ticket), issued
+// once pass 1 has read the current item, so that the prefetched lines wait in
+// L2 for passes 2 and 3 of the current item only.  Measured on the ragged
+// binary32 workload (time per step; DRAM reads of the 10^6-vector case):
+// no prefetch 2.125 ms (1575 MB); the whole next item before the current
+// item 1.99 ms (1719 MB: prefetched lines evicted before use), its first
+// 2, 4 or 8 KiB 2.08, 2.05, 2.02 ms; the whole next item after pass 1
+// 1.93 ms (1592 MB).  Earlier tests with the prefetch before the item: a
+// whole ticket at once or the next ticket taken one ahead were slower.
+// binary64, bound by the FP64 pipe: 0.401 -> 0.388 of the copy bandwidth
+// with the prefetch before the item: off.
 constexpr bool WARP_PREFETCH_F32 = true, WARP_PREFETCH_F64 = false;
 template <typename T>
 __host__ __device__ constexpr bool warp_prefetch() { return sizeof(T) == 4 ? WARP_PREFETCH_F32 : WARP_PREFETCH_F64; }
@@ -205,13 +213,6 @@ __device__ __forceinline__ void prefetch_range_l2(const T* p, int64_t n, int lan
   const char* c = reinterpret_cast<const char*>(p);
   const int64_t bytes = n * (int64_t)sizeof(T);
   for (int64_t b = (int64_t)lane * 128; b < bytes; b += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + b));
-}
-
-// Prefetch vector `vec` of the batch into L2.
-template <typename T>
-__device__ __forceinline__ void prefetch_item_l2(const RaggedArgs<T>& a, int64_t vec, int lane) {
-  const int64_t s = a.off[vec];
-  prefetch_range_l2(a.x + s, a.off[vec + 1] - s, lane);
 }
 
 
@@ -243,9 +244,18 @@ __device__ __forceinline__ void ragged_group_items(const RaggedArgs<T>& a, int l
 template <typename T>
 constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 3 * 256 / B; }
 
+// The descriptors of the items of one warp ticket (in shared memory: the
+// kernel's registers are at their cap).
+struct TicketItems {
+  int64_t s[WARP_BATCH];
+  int32_t n[WARP_BATCH];
+  int32_t vec[WARP_BATCH];
+};
+
 template <typename T, int B>
 __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArgs<T> a) {
   __shared__ BlockShared<T, B> sh;
+  __shared__ TicketItems tk[B / 32];
   const int t = threadIdx.x, lane = t & 31;
   const int nblk = a.sc.counts[LIST_BLOCK], nwarp = a.sc.counts[LIST_WARP], nthr = a.sc.counts[LIST_THREAD];
   const int32_t* Lb = a.sc.items + LIST_BLOCK * a.count;
@@ -266,7 +276,7 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
   }
 
   // warp items, WARP_BATCH per ticket.  binary32 (warp_prefetch) prefetches
-  // the next item of the ticket into L2 while the current item runs.
+  // the next item of the ticket into L2 during the current item.
   for (;;) {
     int base = 0;
     if (lane == 0) base = atomicAdd(&a.sc.tickets[LIST_WARP], WARP_BATCH);
@@ -289,14 +299,27 @@ __global__ void __launch_bounds__(B, ragged_min_blocks<T>(B)) k_ragged(RaggedArg
         warp_forward_stream_batch<T, 2, MAX_LEN, true>(item, nb, lane, a.out);
       }
     } else {
-      for (int j = 0; j < WARP_BATCH && base + j < nwarp; ++j) {
-        const int64_t vec = Lw[base + j];
-        const int64_t s = a.off[vec];
-        const int n = (int)(a.off[vec + 1] - s);
-        if (warp_prefetch<T>() && j + 1 < WARP_BATCH && base + j + 1 < nwarp)
-          prefetch_item_l2(a, Lw[base + j + 1], lane);
-        warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, n, lane, a.out, vec);
+      // the ticket's item descriptors, read by lanes 0 .. WARP_BATCH-1 together
+      TicketItems& d = tk[t >> 5];
+      if (lane < WARP_BATCH && base + lane < nwarp) {
+        const int32_t v = Lw[base + lane];
+        const int64_t s0 = a.off[v];
+        d.vec[lane] = v;
+        d.s[lane] = s0;
+        d.n[lane] = (int)(a.off[v + 1] - s0);
       }
+      __syncwarp();
+      const int nb = nwarp - base < WARP_BATCH ? nwarp - base : WARP_BATCH;
+      for (int j = 0; j < nb; ++j) {
+        const int64_t s = d.s[j];
+        // the next item of the ticket is prefetched into L2 once pass 1 has
+        // read this one (see WARP_PREFETCH_F32)
+        auto prefetch_next = [&]() {
+          if (warp_prefetch<T>() && j + 1 < nb) prefetch_range_l2(a.x + d.s[j + 1], d.n[j + 1], lane);
+        };
+        warp_forward_stream<T>(a.x + s, a.y ? a.y + s : nullptr, d.n[j], lane, a.out, d.vec[j], prefetch_next);
+      }
+      __syncwarp();  // the next ticket rewrites the descriptors
     }
   }
 

@@ -857,15 +857,23 @@ __device__ __forceinline__ void warp_forward_stream_finish(const T* __restrict__
   if (lane == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }
 
+// No work between the passes (warp_forward_stream's default hook).
+struct NoHook {
+  __device__ __forceinline__ void operator()() const {}
+};
+
 // Forward, one warp per vector of any length (5 <= n <= 2^20), three passes
 // over the vector: (1) largest magnitude and zero test, (2) scaled squares,
-// (3) outputs.  yr may be null (norm only).
-template <typename T>
+// (3) outputs.  yr may be null (norm only).  after_pass1() runs once pass 1
+// has read the vector (a caller's prefetch of its next item).
+template <typename T, typename Hook = NoHook>
 __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T* yr, int n, int lane,
-                                                    const VecOut<T>& out, int64_t vec) {
+                                                    const VecOut<T>& out, int64_t vec,
+                                                    const Hook& after_pass1 = Hook()) {
   bool emu, have_s;
   T s;
   const int code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, s, have_s);
+  after_pass1();
   if (code == CODE_ZERO) return;
   if (!have_s) s = stream_pass2_any<T>(xr, n, lane, code, emu);
   const T rt = FP<T>::sqrt(s);
