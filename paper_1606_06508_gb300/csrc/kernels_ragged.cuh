@@ -188,9 +188,8 @@ struct RaggedArgs {
   int64_t count;
 };
 
-// Forward persistent kernel, B threads per block (128 or 256).  Resident
-// threads per SM requested: 5 x 256 for binary32 (at most 48 registers),
-// 3 x 256 for binary64 (at most 80, no spills).
+// Forward persistent kernel, B threads per block (128 or 256), resident
+// threads per SM as ragged_min_blocks asks.
 // L2 prefetch of the next warp item's vector (within the ticket), issued
 // once pass 1 has read the current item, so that the prefetched lines wait in
 // L2 for passes 2 and 3 of the current item only.  Measured on the ragged
@@ -241,8 +240,12 @@ __device__ __forceinline__ void ragged_group_items(const RaggedArgs<T>& a, int l
   }
 }
 
+// Resident threads per SM asked of the persistent forward: 5 x 256 for
+// binary32 (at most 48 registers), 4 x 256 for binary64 (at most 64; 48
+// bytes of spill; against 3 x 256 at 80 registers: ragged binary64 forward
+// 7.29 -> 7.02 ms, forward + backward 1.652 -> 1.630 ms).
 template <typename T>
-constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 3 * 256 / B; }
+constexpr int ragged_min_blocks(int B) { return sizeof(T) == 4 ? 5 * 256 / B : 4 * 256 / B; }
 
 // The descriptors of the items of one warp ticket (in shared memory: the
 // kernel's registers are at their cap).
@@ -377,9 +380,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 8 ? 3 : 1) k_ragged_bwd_warp
 }
 
 // Backward, a group list: one group of W lanes per vector, 32 / W vectors per
-// warp, warp-stride over the list.
+// warp, warp-stride over the list.  Three blocks of 256 per SM (binary64:
+// 80 registers and 16 bytes of spill, against 2 blocks at 104 registers;
+// with the thread kernel below, forward + backward 1.652 -> 1.635 ms).
 template <typename T, int W>
-__global__ void __launch_bounds__(256) k_ragged_bwd_groups(RaggedArgs<T> a, int list) {
+__global__ void __launch_bounds__(256, 3) k_ragged_bwd_groups(RaggedArgs<T> a, int list) {
   constexpr int PER = 32 / W;
   const int lane = threadIdx.x & 31;
   const int cnt = a.sc.counts[list];
@@ -397,9 +402,10 @@ __global__ void __launch_bounds__(256) k_ragged_bwd_groups(RaggedArgs<T> a, int 
   }
 }
 
-// Backward, thread list: one thread per vector, grid-stride over the list.
+// Backward, thread list: one thread per vector, grid-stride over the list
+// (three blocks of 256 per SM, as the group kernel).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ragged_bwd_threads(RaggedArgs<T> a) {
+__global__ void __launch_bounds__(256, 3) k_ragged_bwd_threads(RaggedArgs<T> a) {
   const int nthr = a.sc.counts[LIST_THREAD];
   const int32_t* Lt = a.sc.items + LIST_THREAD * a.count;
   const int stride = (int)((int64_t)gridDim.x * blockDim.x);
