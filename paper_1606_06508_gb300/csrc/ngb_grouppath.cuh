@@ -176,7 +176,8 @@ __device__ __noinline__ void group_backward_slow(const T* __restrict__ yr, const
 // y_k dot on the integer pipes (f64emu::mul_signed) when every one of them is
 // in range, decided from the integer keys of y, g and dot (the same in every
 // lane of the group); otherwise the out-of-line FP64 form redoes the vector.
-// Both give the same bits.
+// With c = 1, part of the products by h go to f64emu::mul as well when
+// grad_h_in_range holds.  Every form gives the same bits.
 template <typename T, int W>
 __device__ __forceinline__ void group_backward(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
                                                int lane, T h, int code) {
@@ -217,20 +218,31 @@ __device__ __forceinline__ void group_backward(const T* __restrict__ yr, const T
       return;
     }
     const uint64_t db = static_cast<uint64_t>(__double_as_longlong(dot));
-    auto t = [&](int c) {  // RN(g_k - RN(y_k dot)) RN-times h
+    // RN(g_k - RN(y_k dot)) RN-times h; with `hemu` the products by h of
+    // chunks c < F64_EMU_GRAD_H_OF_8 by f64emu::mul (see grad_h_in_range)
+    auto t = [&](int c, bool hemu) {
       const double p = __longlong_as_double(
           static_cast<long long>(f64emu::mul_signed(static_cast<uint64_t>(__double_as_longlong(yv[c])), db)));
-      return FP<double>::mul(FP<double>::sub(gv[c], p), h);
+      const double d = FP<double>::sub(gv[c], p);
+      if (hemu && c < F64_EMU_GRAD_H_OF_8)
+        return __longlong_as_double(static_cast<long long>(
+            f64emu::mul(static_cast<uint64_t>(__double_as_longlong(d)), static_cast<uint64_t>(__double_as_longlong(h)))));
+      return FP<double>::mul(d, h);
     };
+    const bool hemu = F64_EMU_GRAD_H_OF_8 > 0 && grad_h_in_range(ry, rg, rd, h);  // group-uniform
     if (code != CODE_ONE) {  // group-uniform; the multiplication by c = 1 is skipped (exact)
       const double cf = factor_of<double, true>(code);
 #pragma unroll
       for (int c = 0; c < 8; ++c)
-        if (W * c + g < n) __stcs(gradr + W * c + g, FP<double>::mul(t(c), cf));
+        if (W * c + g < n) __stcs(gradr + W * c + g, FP<double>::mul(t(c, false), cf));
+    } else if (hemu) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        if (W * c + g < n) __stcs(gradr + W * c + g, t(c, true));
     } else {
 #pragma unroll
       for (int c = 0; c < 8; ++c)
-        if (W * c + g < n) __stcs(gradr + W * c + g, t(c));
+        if (W * c + g < n) __stcs(gradr + W * c + g, t(c, false));
     }
   } else {
     group_backward_tail_hw<T, W>(yv, gv, gradr, n, g, gm, gbase, h, code);

@@ -1087,10 +1087,20 @@ __device__ __noinline__ T bwd_dot_pass_slow(const T* __restrict__ yr, const T* _
   return bwd_dot_pass<T, false>(yr, gr, n, lane, nullptr, nullptr);
 }
 
+// Of every 8 products d_k h of the binary64 backward (d_k = g_k - y_k dot)
+// on the integer-pipe path, how many are formed by f64emu::mul (the rest by
+// the FP64 pipe), as F64_EMU_OUTPUTS_OF_8 for the forward's outputs.
+// Measured on the ragged binary64 forward + backward workload (warp items):
+// 0 / 1 / 2 / 3 / 4 / 8 of 8: 1.609 / 1.593 / 1.580 / 1.570 / 1.561 / 1.582 ms;
+// with the group backward too (group_backward, chunks c < K): 3 / 4 / 5 / 6:
+// 1.563 / 1.553 / 1.550 / 1.555 ms (1.568 at 4 without the groups).
+constexpr int F64_EMU_GRAD_H_OF_8 = 4;
+
 // Backward pass 2: grad_k = ((g_k - y_k dot) h) c.  SCALED = false skips the
 // multiplication by c = 1 (exact, so the same bits).  EMU: y_k dot by
-// f64emu::mul_signed.
-template <typename T, bool SCALED, bool EMU>
+// f64emu::mul_signed.  HEMU (with EMU): F64_EMU_GRAD_H_OF_8 of every 8
+// products d_k h by f64emu::mul (grad_h_in_range holds for the vector).
+template <typename T, bool SCALED, bool EMU, bool HEMU = false>
 __device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
                                               int lane, T dot, T h, T cf) {
   for (int base = 0; base < n; base += 256) {
@@ -1111,7 +1121,13 @@ __device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T*
             static_cast<uint64_t>(__double_as_longlong(a[i])), static_cast<uint64_t>(__double_as_longlong(dot)))));
       else
         p = FP<T>::mul(a[i], dot);
-      T o = FP<T>::mul(FP<T>::sub(b[i], p), h);
+      const T d = FP<T>::sub(b[i], p);
+      T o;
+      if (HEMU && (i & 7) < F64_EMU_GRAD_H_OF_8)  // compile-time per chunk
+        o = __longlong_as_double(static_cast<long long>(
+            f64emu::mul(static_cast<uint64_t>(__double_as_longlong(d)), static_cast<uint64_t>(__double_as_longlong(h)))));
+      else
+        o = FP<T>::mul(d, h);
       if (SCALED) o = FP<T>::mul(o, cf);
       if (k < n) __stcs(gradr + k, o);
     }
@@ -1130,6 +1146,39 @@ __device__ __forceinline__ bool products_in_range(const MagTrack<double>& ta, co
   if (na < (1u << 20) || nb < (1u << 20)) return false;  // a subnormal operand
   const int emin = (int)(na >> 20) + (int)(nb >> 20) - 1023, emax = (int)(ta.k >> 20) + (int)(tb.k >> 20) - 1023;
   return emin >= 1 && emax <= 2045;
+}
+
+// Whether f64emu::mul takes every product d_k h of the backward, with
+// d_k = RN(g_k - p_k), p_k = RN(y_k dot), given the integer keys of y (ry),
+// g (rg) and dot (rd), with products_in_range(ry, rd) already true (every p_k
+// is zero or normal), and h > 0.  Biased exponents: a nonzero p_k lies in
+// [e_y,lo + e_dot - 1023, e_y,hi + e_dot - 1021]; a nonzero difference of
+// two values that are zero or normal with exponents >= E is a multiple of
+// 2^(E - 1075), so its exponent is >= E - 52; and |g_k| + |p_k| is at most
+// twice the largest value of exponent e_hi, which is the largest value of
+// exponent e_hi + 1, so RN(g_k - p_k) stays at or below exponent e_hi + 1.
+// mul() then needs d_k normal and e_d + e_h - 1023 within [1, 2045].
+__device__ __forceinline__ bool grad_h_in_range(const MagTrack<double>& ry, const MagTrack<double>& rg,
+                                                const MagTrack<double>& rd, double h) {
+  const uint32_t hb = (uint32_t)((unsigned long long)__double_as_longlong(h) >> 32);
+  const int eh = (int)(hb >> 20);  // the sign bit is part of eh: a negative h fails below
+  if (eh < 1 || eh > 2046) return false;
+  if (rg.k >= MagTrack<double>::HI_INF) return false;
+  int elo = 4096, ehi = 0;
+  if (rg.k != 0u) {
+    const uint32_t ng = rg.kmin1 + 1u;  // smallest nonzero key of g
+    if (ng < (1u << 20)) return false;  // a subnormal g_k
+    elo = (int)(ng >> 20);
+    ehi = (int)(rg.k >> 20);
+  }
+  if (ry.k != 0u && rd.k != 0u) {
+    const int ed = (int)(rd.k >> 20);
+    elo = min(elo, (int)((ry.kmin1 + 1u) >> 20) + ed - 1023);
+    ehi = max(ehi, (int)(ry.k >> 20) + ed - 1021);
+  }
+  if (ehi == 0) return true;  // every d_k is zero
+  const int dlo = elo - 52, dhi = ehi + 1;
+  return dlo >= 1 && dlo + eh - 1023 >= 1 && dhi + eh - 1023 <= 2045;
 }
 
 // Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),
@@ -1153,7 +1202,10 @@ __device__ __forceinline__ void warp_backward_stream(const T* __restrict__ yr, c
     MagTrack<T> rd;
     rd.take(dot);
     const bool emu = products_in_range(ry, rd);
-    if (emu) {
+    if (emu && F64_EMU_GRAD_H_OF_8 > 0 && grad_h_in_range(ry, rg, rd, h)) {
+      if (code != CODE_ONE) bwd_grad_pass<T, true, true, true>(yr, gr, gradr, n, lane, dot, h, cf);
+      else bwd_grad_pass<T, false, true, true>(yr, gr, gradr, n, lane, dot, h, cf);
+    } else if (emu) {
       if (code != CODE_ONE) bwd_grad_pass<T, true, true>(yr, gr, gradr, n, lane, dot, h, cf);
       else bwd_grad_pass<T, false, true>(yr, gr, gradr, n, lane, dot, h, cf);
     } else {

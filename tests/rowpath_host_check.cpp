@@ -25,6 +25,7 @@
 // Backward paths read y, g (count x n each), h (count) and code (count bytes)
 // and write grad (count x n): warp_bwd (n <= 1024), stream_bwd, block_bwd,
 // group8_bwd, group16_bwd (lengths as the group forward paths).
+// Path ghr: see run_ghr.
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -264,11 +265,63 @@ static int run(int n, const std::string& path, const char* in, const char* outp)
   return 0;
 }
 
+// Path "ghr" (f64): the decision of grad_h_in_range against brute force.
+// Reads count rows of y (n values), g (n values), dot (1) and h (1), all
+// binary64 in that order per array (y of every row, then g, dot, h), and
+// writes count bytes: 0 when products_in_range(keys of y, key of dot) fails
+// (the decision is not taken), else 1 + the decision; then count bytes: 1
+// when every d_k = RN(g_k - RN(y_k dot)) satisfies f64emu::mul_in_range(d_k, h).
+static int run_ghr(int n, const char* inp, const char* outp) {
+  FILE* f = fopen(inp, "rb");
+  if (!f) { perror(inp); return 2; }
+  fseek(f, 0, SEEK_END);
+  const long bytes = ftell(f);
+  fseek(f, 0, SEEK_SET);
+  const long count = bytes / (long)((2 * n + 2) * sizeof(double));
+  std::vector<double> y((size_t)count * n), g((size_t)count * n), dot(count), h(count);
+  auto rd = [&](void* p, size_t b) {
+    if (b && fread(p, 1, b, f) != b) { fprintf(stderr, "short read\n"); exit(2); }
+  };
+  rd(y.data(), y.size() * sizeof(double));
+  rd(g.data(), g.size() * sizeof(double));
+  rd(dot.data(), dot.size() * sizeof(double));
+  rd(h.data(), h.size() * sizeof(double));
+  fclose(f);
+  std::vector<unsigned char> decision(count), brute(count);
+  for (long i = 0; i < count; ++i) {
+    MagTrack<double> ry, rg, rdot;
+    for (int k = 0; k < n; ++k) {
+      ry.take(y[(size_t)i * n + k]);
+      rg.take(g[(size_t)i * n + k]);
+    }
+    rdot.take(dot[i]);
+    decision[i] = products_in_range(ry, rdot) ? (unsigned char)(1 + (grad_h_in_range(ry, rg, rdot, h[i]) ? 1 : 0)) : 0;
+    bool all = true;
+    for (int k = 0; k < n; ++k) {
+      volatile double p = y[(size_t)i * n + k] * dot[i];
+      volatile double d = g[(size_t)i * n + k] - p;
+      uint64_t db, hb;
+      const double dv = d, hv = h[i];
+      memcpy(&db, &dv, 8);
+      memcpy(&hb, &hv, 8);
+      all = all && f64emu::mul_in_range(db, hb);
+    }
+    brute[i] = all ? 1 : 0;
+  }
+  FILE* o = fopen(outp, "wb");
+  if (!o) { perror(outp); return 2; }
+  fwrite(decision.data(), 1, count, o);
+  fwrite(brute.data(), 1, count, o);
+  fclose(o);
+  return 0;
+}
+
 int main(int argc, char** argv) {
   if (argc != 6) {
     fprintf(stderr, "usage: %s f32|f64 n path in out\n", argv[0]);
     return 2;
   }
+  if (!strcmp(argv[3], "ghr")) return run_ghr(atoi(argv[2]), argv[4], argv[5]);
   const int n = atoi(argv[2]);
   if (n < 5 || n > MAX_LEN) { fprintf(stderr, "n must be in 5..2^20\n"); return 2; }
   return !strcmp(argv[1], "f32") ? run<float>(n, argv[3], argv[4], argv[5]) : run<double>(n, argv[3], argv[4], argv[5]);

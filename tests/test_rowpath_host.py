@@ -128,6 +128,79 @@ def test_f64_backward_integer_pipe_limits(rph, n, path):
     _backward(rph, "f64", n, path, x, f"f64 limits n={n} {path}")
 
 
+def test_grad_h_in_range_against_brute_force(rph):
+    """grad_h_in_range (the binary64 backward's choice of f64emu::mul for
+    d_k h, d_k = RN(g_k - RN(y_k dot))) is never true for a row with a d_k
+    outside mul()'s range.  Rows over the whole exponent range, with
+    adversarial components: g_k = p_k (d_k = 0), g_k one ulp away from p_k
+    (the smallest nonzero d_k), subnormal and huge g_k, zero y and dot, and
+    rows whose d_k h sits on the upper limit."""
+    n, cnt = 6, 40000
+    rng = np.random.default_rng(11)
+    sy = rng.integers(-1100, 1, size=(cnt, 1))
+    y = rng.uniform(1, 2, size=(cnt, n)) * np.sign(rng.standard_normal((cnt, n))) * 2.0 ** sy
+    y[rng.uniform(size=(cnt, n)) < 0.1] = 0.0
+    dot = rng.uniform(1, 2, size=cnt) * np.sign(rng.standard_normal(cnt)) * 2.0 ** rng.integers(-1080, 1024, size=cnt)
+    dot[::50] = 0.0
+    g = rng.uniform(1, 2, size=(cnt, n)) * np.sign(rng.standard_normal((cnt, n))) * \
+        2.0 ** rng.integers(-1100, 1023, size=(cnt, 1)) * 2.0 ** rng.integers(-40, 1, size=(cnt, n))
+    with np.errstate(over="ignore", under="ignore"):
+        p = y * dot[:, None]
+        for i in range(cnt):
+            k = int(rng.integers(n))
+            kind = i % 4
+            if kind == 0:
+                g[i, k] = p[i, k]
+            elif kind == 1:
+                g[i, k] = np.nextafter(p[i, k], np.inf)
+            elif kind == 2:
+                g[i, k] = np.nextafter(p[i, k], -np.inf)
+    h = rng.uniform(1, 2, size=cnt) * 2.0 ** rng.integers(-1022, 1024, size=cnt)
+    g = np.where(np.isfinite(g), g, 0.0)
+    # the upper edge: g_k near the top of binade E and p_k = y_k dot of the
+    # opposite sign with its bound in binade E too, so that d_k reaches binade
+    # E + 1; h puts E + 1 + e_h - 1023 just below, on and above 2045
+    up = []
+    for E in range(1030, 2041, 10):
+        for eh in range(3064 - E, 3070 - E):
+            yy = np.full(n, 2.0 ** -10)
+            yy[0] = 1.99
+            gg = np.full(n, 2.0 ** (E - 1023 - 30))
+            gg[0] = 1.99 * 2.0 ** (E - 1023)
+            up.append((yy, gg, -1.99 * 2.0 ** (E - 2 - 1023), 2.0 ** (eh - 1023)))
+    y = np.concatenate([y, np.array([u[0] for u in up])])
+    g = np.concatenate([g, np.array([u[1] for u in up])])
+    dot = np.concatenate([dot, np.array([u[2] for u in up])])
+    h = np.concatenate([h, np.array([u[3] for u in up])])
+    cnt = dot.size
+    raw = _call(rph, "f64", n, "ghr", [y.reshape(-1), g.reshape(-1), dot, h])
+    decision, brute = raw[:cnt], raw[cnt:]
+    taken = decision == 2
+    assert not np.any(taken & (brute == 0)), np.flatnonzero(taken & (brute == 0))[:10]
+    assert taken.sum() > cnt // 20 and (decision == 1).sum() > cnt // 20  # both answers occur
+    tail = slice(cnt - len(up), cnt)  # the edge rows hold both answers of the brute force
+    assert np.any(brute[tail] == 1) and np.any(brute[tail] == 0)
+
+
+@pytest.mark.parametrize("n", [40, 300, 1025])
+def test_f64_backward_product_by_h_over_the_exponent_range(rph, n):
+    """The streaming binary64 backward (the ragged warp items) on inputs and
+    upstream gradients over the whole exponent range, so that the products
+    d_k h fall inside and outside f64emu::mul's range, row by row."""
+    rng = np.random.default_rng(5 * n)
+    cnt = 56
+    sx = np.array([-1000, -600, -200, 0, 200, 600, 1000])
+    sg = np.array([-1074, -1060, -1022, -1000, -900, -600, -300, 0, 300, 600, 900, 1000, 1015])
+    x = rng.standard_normal((cnt, n)) * 2.0 ** sx[np.arange(cnt) % sx.size][:, None]
+    oy, _, oh, oc = oracle.normalize(x.reshape(-1), dim=n)
+    g = rng.standard_normal((cnt, n)) * 2.0 ** sg[(np.arange(cnt) * 5) % sg.size][:, None]
+    g[::3, 0] = 2.0 ** 1000
+    g[1::3, 1] = 5e-324
+    g = g.reshape(-1)
+    raw = _call(rph, "f64", n, "stream_bwd", [oy, g, oh, oc.astype(np.int8)])
+    assert_bits(raw.view(np.float64), oracle.backward(oy, g, oh, oc, dim=n), f"f64 n={n} product by h")
+
+
 def _group_lengths(cnt, n):
     return np.maximum(5, n - np.arange(cnt) % 5)
 
@@ -171,6 +244,33 @@ def test_group_forward_and_backward_match_oracle(rph, f, n, w, cnt):
         og = oracle.backward(oy, _pack(g, lengths), oh, oc, dim=0, offsets=off)
         rawb = _call(rph, f, n, f"group{w}_bwd", [yr, g, oh, oc.astype(np.int8)])
         assert_bits(_pack(rawb.view(dt).reshape(c_, n), lengths), og, what + " grad")
+
+
+@pytest.mark.parametrize("n,w", [(64, 8), (128, 16)])
+def test_group_backward_product_by_h_over_the_exponent_range(rph, n, w):
+    """binary64 group backward on inputs and upstream gradients over the whole
+    exponent range (the products d_k h inside and outside f64emu::mul's
+    range, group by group within a warp)."""
+    rng = np.random.default_rng(3 * n + w)
+    cnt = 56
+    sx = np.array([-1000, -600, -200, 0, 200, 600, 1000])
+    sg = np.array([-1074, -1060, -1022, -1000, -900, -600, -300, 0, 300, 600, 900, 1000, 1015])
+    x = rng.standard_normal((cnt, n)) * 2.0 ** sx[np.arange(cnt) % sx.size][:, None]
+    lengths = _group_lengths(cnt, n)
+    for i, m in enumerate(lengths):
+        x[i, m:] = 0
+    off = synth.offsets_from_lengths(lengths)
+    oy, _, oh, oc = oracle.normalize(_pack(x, lengths), dim=0, offsets=off)
+    g = rng.standard_normal((cnt, n)) * 2.0 ** sg[(np.arange(cnt) * 5) % sg.size][:, None]
+    g[::3, 0] = 2.0 ** 1000
+    g[1::3, 1] = 5e-324
+    yr = np.zeros((cnt, n))
+    for i, m in enumerate(lengths):
+        yr[i, :m] = oy[off[i]:off[i + 1]]
+        g[i, m:] = 0
+    og = oracle.backward(oy, _pack(g, lengths), oh, oc, dim=0, offsets=off)
+    rawb = _call(rph, "f64", n, f"group{w}_bwd", [yr, g, oh, oc.astype(np.int8)])
+    assert_bits(_pack(rawb.view(np.float64).reshape(cnt, n), lengths), og, f"f64 group{w} product by h")
 
 
 @pytest.mark.parametrize("n", [1025, 5000])
