@@ -174,6 +174,69 @@ NGB_HD uint64_t add_nonneg(uint64_t a, uint64_t b, bool& ok) {
   return ((uint64_t)(uint32_t)(Eb - 1 + c) << 52) + sig;
 }
 
+// Count of leading zero bits of v != 0.
+NGB_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)v);
+#else
+  return __builtin_clzll(v);
+#endif
+}
+
+// a + b for finite a, b of either sign (zero and subnormal included), rounded
+// to nearest even, when the larger magnitude has a biased exponent of at most
+// 2045 (the caller's range test: the sum cannot overflow).
+//
+// The operands are ordered by magnitude and aligned as in add_nonneg (10
+// guard bits, the bits shifted out ORed into bit 0).  Same signs: the
+// significands are added as there.  Opposite signs: the smaller is
+// subtracted from the larger (the difference is >= 0) and the result is
+// shifted left until its leading one is back at bit 62, or until the
+// exponent reaches that of 2^-1022 (a subnormal result).  Two cases:
+//   - exponent difference 0 or 1: no bit was shifted out, the difference is
+//     exact and is only rounded;
+//   - difference >= 2: the larger significand has its leading one at bit 62
+//     and the aligned smaller one is below 2^61, so the difference keeps its
+//     leading one at bit 62 or 61: at most one shift, and at least 9 of the
+//     10 guard bits are rounded off.  The exact difference M - A - e
+//     (0 < e < 1 in units of bit 0, when bits were lost) lies strictly
+//     between two integers; the computed M - (A | 1) is the odd one of them
+//     or its odd neighbour below, so no multiple of 2^8 -- a rounding
+//     boundary or a tie -- lies between the computed and the exact value, or
+//     on the computed one: both round the same way.
+// A difference of zero is +0 (round to nearest).
+NGB_HD uint64_t add_signed(uint64_t a, uint64_t b) {
+  const uint64_t SIGN = uint64_t(1) << 63;
+  const uint64_t ma = a & ~SIGN, mbv = b & ~SIGN;
+  const bool swap = mbv > ma;
+  const uint64_t big = swap ? mbv : ma, small = swap ? ma : mbv;
+  const uint64_t sign = (swap ? b : a) & SIGN;
+  const int eb = (int)(big >> 52), es = (int)(small >> 52);
+  const uint64_t mb = (big & FRAC) | ((uint64_t)(eb != 0 ? 1u : 0u) << 52);
+  const uint64_t ms = (small & FRAC) | ((uint64_t)(es != 0 ? 1u : 0u) << 52);
+  const int Eb = eb > 1 ? eb : 1;  // subnormals have the exponent of 2^-1022
+  const int Es = es > 1 ? es : 1;
+  int d = Eb - Es;
+  d = d < 63 ? d : 63;
+  const uint64_t s10 = ms << 10;
+  const uint64_t lost = s10 & ((uint64_t(1) << d) - 1u);
+  const uint64_t al = (s10 >> d) | (lost != 0 ? 1u : 0u);
+  const uint64_t M = mb << 10;
+  if (((a ^ b) & SIGN) == 0) {  // same signs
+    const uint64_t sum = M + al;  // < 2^64 - 2^11
+    const int c = (int)(sum >> 63);
+    const uint64_t sig = round_shift(sum, 10 + c);
+    return sign | (((uint64_t)(uint32_t)(Eb - 1 + c) << 52) + sig);
+  }
+  uint64_t diff = M - al;
+  if (diff == 0) return 0;
+  const int lz = clz64(diff) - 1;  // shift that puts the leading one at bit 62
+  const int sh = lz < Eb - 1 ? lz : Eb - 1;
+  diff <<= sh;
+  const uint64_t sig = round_shift(diff, 10);
+  return sign | (((uint64_t)(uint32_t)(Eb - sh - 1) << 52) + sig);
+}
+
 // High 64 bits of the 128-bit product a b.
 NGB_HD uint64_t mulhi64(uint64_t a, uint64_t b) {
 #if defined(__CUDA_ARCH__)

@@ -219,11 +219,19 @@ __device__ __forceinline__ void group_backward(const T* __restrict__ yr, const T
     }
     const uint64_t db = static_cast<uint64_t>(__double_as_longlong(dot));
     // RN(g_k - RN(y_k dot)) RN-times h; with `hemu` the products by h of
-    // chunks c < F64_EMU_GRAD_H_OF_8 by f64emu::mul (see grad_h_in_range)
+    // chunks c < F64_EMU_GRAD_H_OF_8 by f64emu::mul and the differences of
+    // chunks c >= 8 - F64_EMU_GRAD_SUB_OF_8 by f64emu::add_signed (see
+    // grad_h_in_range)
     auto t = [&](int c, bool hemu) {
       const double p = __longlong_as_double(
           static_cast<long long>(f64emu::mul_signed(static_cast<uint64_t>(__double_as_longlong(yv[c])), db)));
-      const double d = FP<double>::sub(gv[c], p);
+      double d;
+      if (hemu && c >= 8 - F64_EMU_GRAD_SUB_OF_8)
+        d = __longlong_as_double(static_cast<long long>(
+            f64emu::add_signed(static_cast<uint64_t>(__double_as_longlong(gv[c])),
+                               static_cast<uint64_t>(__double_as_longlong(p)) ^ 0x8000000000000000ull)));
+      else
+        d = FP<double>::sub(gv[c], p);
       if (hemu && c < F64_EMU_GRAD_H_OF_8)
         return __longlong_as_double(static_cast<long long>(
             f64emu::mul(static_cast<uint64_t>(__double_as_longlong(d)), static_cast<uint64_t>(__double_as_longlong(h)))));

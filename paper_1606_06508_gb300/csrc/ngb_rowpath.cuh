@@ -1095,11 +1095,19 @@ __device__ __noinline__ T bwd_dot_pass_slow(const T* __restrict__ yr, const T* _
 // with the group backward too (group_backward, chunks c < K): 3 / 4 / 5 / 6:
 // 1.563 / 1.553 / 1.550 / 1.555 ms (1.568 at 4 without the groups).
 constexpr int F64_EMU_GRAD_H_OF_8 = 4;
+// Of every 8 differences d_k = RN(g_k - p_k) of that path, how many are
+// formed by f64emu::add_signed (the upper chunks, i mod 8 >= 8 - K).
+// Measured on the same workload (with the products by h at 4 of 8):
+// 0 / 2 / 4 / 6 of 8: 1.553 / 1.595 / 1.690 / 1.853 ms -- the signed sum's
+// alignment, normalization and rounding load the ALU more than the DADD it
+// replaces loads the FP64 pipe, so none is taken.
+constexpr int F64_EMU_GRAD_SUB_OF_8 = 0;
 
 // Backward pass 2: grad_k = ((g_k - y_k dot) h) c.  SCALED = false skips the
 // multiplication by c = 1 (exact, so the same bits).  EMU: y_k dot by
 // f64emu::mul_signed.  HEMU (with EMU): F64_EMU_GRAD_H_OF_8 of every 8
-// products d_k h by f64emu::mul (grad_h_in_range holds for the vector).
+// products d_k h by f64emu::mul and F64_EMU_GRAD_SUB_OF_8 of every 8
+// differences by f64emu::add_signed (grad_h_in_range holds for the vector).
 template <typename T, bool SCALED, bool EMU, bool HEMU = false>
 __device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
                                               int lane, T dot, T h, T cf) {
@@ -1121,7 +1129,13 @@ __device__ __forceinline__ void bwd_grad_pass(const T* __restrict__ yr, const T*
             static_cast<uint64_t>(__double_as_longlong(a[i])), static_cast<uint64_t>(__double_as_longlong(dot)))));
       else
         p = FP<T>::mul(a[i], dot);
-      const T d = FP<T>::sub(b[i], p);
+      T d;
+      if (HEMU && (i & 7) >= 8 - F64_EMU_GRAD_SUB_OF_8)  // compile-time per chunk
+        d = __longlong_as_double(static_cast<long long>(
+            f64emu::add_signed(static_cast<uint64_t>(__double_as_longlong(b[i])),
+                               static_cast<uint64_t>(__double_as_longlong(p)) ^ 0x8000000000000000ull)));
+      else
+        d = FP<T>::sub(b[i], p);
       T o;
       if (HEMU && (i & 7) < F64_EMU_GRAD_H_OF_8)  // compile-time per chunk
         o = __longlong_as_double(static_cast<long long>(
@@ -1178,7 +1192,8 @@ __device__ __forceinline__ bool grad_h_in_range(const MagTrack<double>& ry, cons
   }
   if (ehi == 0) return true;  // every d_k is zero
   const int dlo = elo - 52, dhi = ehi + 1;
-  return dlo >= 1 && dlo + eh - 1023 >= 1 && dhi + eh - 1023 <= 2045;
+  // ehi <= 2045 also lets f64emu::add_signed form every d_k (no overflow)
+  return ehi <= 2045 && dlo >= 1 && dlo + eh - 1023 >= 1 && dhi + eh - 1023 <= 2045;
 }
 
 // Backward, one warp per vector of any length: (1) dot = CR(y_k g_k),

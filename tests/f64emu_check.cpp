@@ -1,4 +1,4 @@
-// Host check of the integer-pipe binary64 square, product, sum, square root,
+// Host check of the integer-pipe binary64 square, product, sums, square root,
 // reciprocal and power-of-two scaling (csrc/ngb_f64emu.cuh) against the host's
 // IEEE 754 binary64 multiply, add, divide and square root (round to nearest
 // even).  Prints "<cases> <in range> <mismatches>" per operation; any mismatch
@@ -91,6 +91,44 @@ int main(int argc, char** argv) {
                                  (unsigned long long)q, (unsigned long long)s, (unsigned long long)bits(ref));
         ++add_bad;
       }
+    }
+  }
+  // signed sums: operands of either sign, d binades apart (d in [-2, 70]),
+  // equal magnitudes, one-ulp neighbours (cancellation down to the last bit),
+  // subnormals and zeros of either sign, half-ulp ties; larger exponent <= 2045
+  long sadd_bad = 0;
+  for (long i = 0; i < n; ++i) {
+    const int eb = (int)(next64() % 2046);
+    const int mode = (int)(next64() % 6);
+    uint64_t p = make(eb, (int)(next64() % 6)), q;
+    if (mode == 0) {
+      int es = eb - ((int)(next64() % 73) - 2);
+      es = es < 0 ? 0 : (es > 2045 ? 2045 : es);
+      q = make(es, (int)(next64() % 6));
+    } else if (mode == 1) {
+      q = next64() & ngb::f64emu::FRAC;
+      if (next64() & 1) p = next64() & ngb::f64emu::FRAC;
+    } else if (mode == 2) {
+      q = (next64() & 1) ? 0 : p;
+    } else if (mode == 3) {
+      q = p + (uint64_t)((int)(next64() % 5) - 2);  // neighbours: massive cancellation
+      if ((q >> 52) > 2045) q = p;
+    } else if (mode == 4) {
+      int es = eb - 53 + (int)(next64() % 3) - 1;
+      if (es < 1) es = 1;
+      q = ((uint64_t)es << 52) | ((next64() % 3 == 0) ? 0 : (next64() & 1));
+    } else {
+      q = make(eb, (int)(next64() % 6));
+    }
+    if (next64() & 1) p |= uint64_t(1) << 63;
+    if (next64() & 1) q |= uint64_t(1) << 63;
+    if (next64() & 1) { const uint64_t t = p; p = q; q = t; }
+    const uint64_t s = ngb::f64emu::add_signed(p, q);
+    const double ref = val(p) + val(q);
+    if (s != bits(ref)) {
+      if (sadd_bad < 5) fprintf(stderr, "add_signed %016llx + %016llx: %016llx vs %016llx\n", (unsigned long long)p,
+                                (unsigned long long)q, (unsigned long long)s, (unsigned long long)bits(ref));
+      ++sadd_bad;
     }
   }
   long mul_fast = 0, mul_bad = 0;
@@ -197,5 +235,6 @@ int main(int argc, char** argv) {
   printf("mul_signed %ld %ld %ld\n", n, smul_fast, smul_bad);
   printf("mul %ld %ld %ld\n", n, mul_fast, mul_bad);
   printf("add %ld %ld %ld\n", n, add_fast, add_bad);
-  return (sq_bad || add_bad || mul_bad || smul_bad || sr_bad || rc_bad || ld_bad) ? 1 : 0;
+  printf("add_signed %ld %ld %ld\n", n, n, sadd_bad);
+  return (sq_bad || add_bad || sadd_bad || mul_bad || smul_bad || sr_bad || rc_bad || ld_bad) ? 1 : 0;
 }

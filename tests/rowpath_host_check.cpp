@@ -270,7 +270,8 @@ static int run(int n, const std::string& path, const char* in, const char* outp)
 // binary64 in that order per array (y of every row, then g, dot, h), and
 // writes count bytes: 0 when products_in_range(keys of y, key of dot) fails
 // (the decision is not taken), else 1 + the decision; then count bytes: 1
-// when every d_k = RN(g_k - RN(y_k dot)) satisfies f64emu::mul_in_range(d_k, h).
+// when every d_k = RN(g_k - RN(y_k dot)) satisfies f64emu::mul_in_range(d_k, h)
+// and no g_k or p_k exceeds biased exponent 2045 (f64emu::add_signed's range).
 static int run_ghr(int n, const char* inp, const char* outp) {
   FILE* f = fopen(inp, "rb");
   if (!f) { perror(inp); return 2; }
@@ -304,7 +305,12 @@ static int run_ghr(int n, const char* inp, const char* outp) {
       const double dv = d, hv = h[i];
       memcpy(&db, &dv, 8);
       memcpy(&hb, &hv, 8);
-      all = all && f64emu::mul_in_range(db, hb);
+      uint64_t gb, pb;
+      const double gv = g[(size_t)i * n + k], pv = p;
+      memcpy(&gb, &gv, 8);
+      memcpy(&pb, &pv, 8);
+      // f64emu::add_signed forms d_k when neither operand exceeds exponent 2045
+      all = all && f64emu::mul_in_range(db, hb) && ((gb >> 52) & 0x7FF) <= 2045 && ((pb >> 52) & 0x7FF) <= 2045;
     }
     brute[i] = all ? 1 : 0;
   }

@@ -38,6 +38,8 @@ def test_square_and_sum_match_ieee(checker, seed):
     assert bad == 0 and taken > cases // 2
     cases, taken, bad = rows["add"]
     assert bad == 0 and taken > cases // 2
+    cases, taken, bad = rows["add_signed"]
+    assert bad == 0 and taken == cases
     cases, taken, bad = rows["sqrt"]
     assert bad == 0 and taken == cases
     cases, taken, bad = rows["rcp"]

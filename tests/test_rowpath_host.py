@@ -130,8 +130,9 @@ def test_f64_backward_integer_pipe_limits(rph, n, path):
 
 def test_grad_h_in_range_against_brute_force(rph):
     """grad_h_in_range (the binary64 backward's choice of f64emu::mul for
-    d_k h, d_k = RN(g_k - RN(y_k dot))) is never true for a row with a d_k
-    outside mul()'s range.  Rows over the whole exponent range, with
+    d_k h and of f64emu::add_signed for d_k = RN(g_k - RN(y_k dot))) is never
+    true for a row with a d_k outside mul()'s range or a g_k, p_k outside
+    add_signed()'s.  Rows over the whole exponent range, with
     adversarial components: g_k = p_k (d_k = 0), g_k one ulp away from p_k
     (the smallest nonzero d_k), subnormal and huge g_k, zero y and dot, and
     rows whose d_k h sits on the upper limit."""
@@ -168,6 +169,13 @@ def test_grad_h_in_range_against_brute_force(rph):
             gg = np.full(n, 2.0 ** (E - 1023 - 30))
             gg[0] = 1.99 * 2.0 ** (E - 1023)
             up.append((yy, gg, -1.99 * 2.0 ** (E - 2 - 1023), 2.0 ** (eh - 1023)))
+    # g_k in the top binade (exponent 2046), products by a small h in range:
+    # add_signed's limit decides
+    for eh in (1000, 990, 900):
+        yy = np.full(n, 0.5)
+        gg = np.full(n, 2.0 ** 1000)
+        gg[1] = 1.5 * 2.0 ** 1023
+        up.append((yy, gg, 0.75, 2.0 ** (eh - 1023)))
     y = np.concatenate([y, np.array([u[0] for u in up])])
     g = np.concatenate([g, np.array([u[1] for u in up])])
     dot = np.concatenate([dot, np.array([u[2] for u in up])])
