@@ -318,6 +318,10 @@ __global__ void __launch_bounds__(256) k_rows_warp_bwd(const T* __restrict__ y, 
 // and shares one square root and reciprocal among them.
 constexpr int F64_ROW_BATCH = 4;
 
+// The dense binary64 row batch forms 3 of every 8 outputs on the integer
+// pipe (see F64_EMU_OUTPUTS_OF_8).
+constexpr int F64_EMU_OUTPUTS_OF_8_ROWS = 3;
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) k_rows_stream_batch(const T* __restrict__ x, T* y, VecOut<T> out,
                                                             int64_t count, int n) {
@@ -332,7 +336,7 @@ __global__ void __launch_bounds__(256) k_rows_stream_batch(const T* __restrict__
       yr = y ? y + vec * n : nullptr;
       nn = n;
     };
-    warp_forward_stream_batch<T, NB, MAX_LEN>(item, nb, lane, out);
+    warp_forward_stream_batch<T, NB, MAX_LEN, false, F64_EMU_OUTPUTS_OF_8_ROWS>(item, nb, lane, out);
   }
 }
 

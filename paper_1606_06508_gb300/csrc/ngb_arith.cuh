@@ -216,6 +216,9 @@ template <> struct Pow2Scale<double> {
 // two pipes run side by side, and this split balances them.  Measured (0 to
 // 8 of 8): ragged binary64 0.40 / 0.42 / 0.43 / 0.42 / 0.41 / 0.34 / 0.33 of
 // the copy bandwidth at 0 / 1 / 2 / 3 / 4 / 6 / 8; dense rows 0.44 at 2 and 4.
+// (The dense binary64 row batch takes 3: rows of 256, 2^19 rows, 0.739 ms at
+// 2 and 0.712 ms at 3, while the ragged binary64 workloads are fastest at 2:
+// forward 6.96 / 7.00 / 7.03 ms at 2 / 1 / 3.)
 constexpr int F64_EMU_OUTPUTS_OF_8 = 2;
 
 template <typename T, int N, bool EMU> struct Chunk {
@@ -227,6 +230,7 @@ template <typename T, int N, bool EMU> struct Chunk {
 #pragma unroll
     for (int i = 0; i < N; ++i) q[i] = FP<T>::mul(v[i], v[i]);
   }
+  template <int K = F64_EMU_OUTPUTS_OF_8>
   __device__ __forceinline__ static T output(int /*i*/, T h, T v) { return FP<T>::mul(h, v); }
 };
 template <int N> struct Chunk<double, N, true> {
@@ -249,8 +253,10 @@ template <int N> struct Chunk<double, N, true> {
   }
   // x^ = RN(h x~) for chunk position i (h = 1/r~ lies in [2^-511, 2^482] and
   // h x~ in [2^-1022, 1] for these vectors, inside f64emu::mul's range)
+  // (K of every 8 by f64emu::mul: F64_EMU_OUTPUTS_OF_8 unless a kernel asks otherwise)
+  template <int K = F64_EMU_OUTPUTS_OF_8>
   __device__ __forceinline__ static double output(int i, double h, double v) {
-    if ((i & 7) < F64_EMU_OUTPUTS_OF_8)
+    if ((i & 7) < K)
       return __longlong_as_double(static_cast<long long>(
           f64emu::mul(static_cast<uint64_t>(__double_as_longlong(v)), static_cast<uint64_t>(__double_as_longlong(h)))));
     return __dmul_rn(h, v);

@@ -79,7 +79,7 @@ __device__ __forceinline__ void group_forward_tail(T (&v)[8], T* yr, int n, int 
   if (yr) {
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-      if (W * c + g < n) __stcs(yr + W * c + g, Chunk<T, 8, EMU>::output(c, h, v[c]));
+      if (W * c + g < n) __stcs(yr + W * c + g, Chunk<T, 8, EMU>::template output<>(c, h, v[c]));
   }
   if (g == 0) out.put(vec, FP<T>::mul(inverse_of<T, true>(code), rt), h, code);
 }

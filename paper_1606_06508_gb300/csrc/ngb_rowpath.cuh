@@ -560,8 +560,9 @@ constexpr int STREAM_ROUNDS = 3;
 // accumulated in ascending c.  Tree: strides 128, 64, 32 inside the lane,
 // 16 .. 1 by shuffles.  Nothing of the vector is held between passes: each
 // pass reads it again (the second and third reads usually hit L2).
+// The in-lane levels (strides 128, 64, 32): lane l's partial sum of slot l.
 template <typename T>
-__device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
+__device__ __forceinline__ T stream_tree_lane(T (&acc)[8], int n, int lane) {
   const int used = n < CR_SLOTS ? n : CR_SLOTS;
 #pragma unroll
   for (int p = 4; p >= 1; p >>= 1) {
@@ -570,17 +571,52 @@ __device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
     for (int i = 0; i < p; ++i)
       if (32 * (i + p) + lane < used) acc[i] = FP<T>::add(acc[i], acc[i + p]);
   }
+  return acc[0];
+}
+
+// The shuffle levels (strides 16 .. 1) on the lane partials v; the total is
+// returned to every lane.
+template <typename T>
+__device__ __forceinline__ T stream_tree_shfl(T v, int n, int lane) {
+  const int used = n < CR_SLOTS ? n : CR_SLOTS;
   if (used == CR_SLOTS) {  // butterfly: every lane ends with the total
 #pragma unroll
-    for (int p = 16; p >= 1; p >>= 1) acc[0] = FP<T>::add(acc[0], __shfl_xor_sync(FULL, acc[0], p));
-    return acc[0];
+    for (int p = 16; p >= 1; p >>= 1) v = FP<T>::add(v, __shfl_xor_sync(FULL, v, p));
+    return v;
   }
 #pragma unroll
   for (int p = 16; p >= 1; p >>= 1) {
-    const T o = __shfl_xor_sync(FULL, acc[0], p);
-    if (lane < p && lane + p < used) acc[0] = FP<T>::add(acc[0], o);
+    const T o = __shfl_xor_sync(FULL, v, p);
+    if (lane < p && lane + p < used) v = FP<T>::add(v, o);
   }
-  return __shfl_sync(FULL, acc[0], 0);
+  return __shfl_sync(FULL, v, 0);
+}
+
+// The shuffle levels for two vectors at once: a and b are the lane partials
+// of vectors A (na components) and B (nb).  The first exchange leaves slot
+// i + 16 added into slot i of A in lane i and of B in lane 16 + i (i < 16);
+// the remaining levels run inside each half-warp and serve both vectors with
+// one instruction.  The additions and their order are those of CR(n) for each
+// vector.  Returns A's total in lane 0 and B's in lane 16.
+template <typename T>
+__device__ __forceinline__ T stream_tree_shfl2(T a, int na, T b, int nb, int lane) {
+  const bool hi = lane >= 16;
+  const int i = lane & 15;
+  const int used = hi ? (nb < CR_SLOTS ? nb : CR_SLOTS) : (na < CR_SLOTS ? na : CR_SLOTS);
+  const T o16 = __shfl_xor_sync(FULL, hi ? a : b, 16);  // lane i gets A's slot i + 16, lane 16 + i B's slot i
+  T r = hi ? b : a;
+  if (i + 16 < used) r = FP<T>::add(r, o16);
+#pragma unroll
+  for (int p = 8; p >= 1; p >>= 1) {
+    const T o = __shfl_xor_sync(FULL, r, p);
+    if (i < p && i + p < used) r = FP<T>::add(r, o);
+  }
+  return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T stream_tree(T (&acc)[8], int n, int lane) {
+  return stream_tree_shfl<T>(stream_tree_lane<T>(acc, n, lane), n, lane);
 }
 
 // Eight chunks of one round; rounds that lie inside the vector skip the
@@ -601,7 +637,9 @@ __device__ __forceinline__ void stream_load8(const T* __restrict__ p, int base, 
 
 // Pass 2 of the forward: the scaled squares in the order CR(n).  SCALED
 // selects x~ = c x; otherwise x~ = x (c = 1).
-template <typename T, bool SCALED, bool EMU, bool TAIL_SKIP = true>
+// LANE: return lane l's partial sum after the in-lane levels only (the
+// shuffle levels left to the caller, stream_tree_shfl2).
+template <typename T, bool SCALED, bool EMU, bool TAIL_SKIP = true, bool LANE = false>
 __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n, int lane, T cf, int E) {
   T acc[8];
 #pragma unroll
@@ -633,11 +671,12 @@ __device__ __forceinline__ T stream_sum_squares(const T* __restrict__ xr, int n,
       if (base + 32 * i + lane < n) acc[i] = FP<T>::add(acc[i], q[i]);
     }
   }
+  if (LANE) return stream_tree_lane<T>(acc, n, lane);
   return stream_tree<T>(acc, n, lane);
 }
 
 // Pass 3 of the forward: x^ = h x~, written with evict-first stores.
-template <typename T, bool SCALED, bool EMU>
+template <typename T, bool SCALED, bool EMU, int OUTK = F64_EMU_OUTPUTS_OF_8>
 __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, int n, int lane, T h, T cf, int E) {
   int base = 0;
   if (sizeof(T) == 4) {  // binary32: STREAM_ROUNDS rounds of loads in flight
@@ -654,7 +693,7 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
         if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v[r]);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          __stcs(yr + base + 256 * r + 32 * i + lane, Chunk<T, 8, EMU>::output(i, h, v[r][i]));
+          __stcs(yr + base + 256 * r + 32 * i + lane, Chunk<T, 8, EMU>::template output<OUTK>(i, h, v[r][i]));
       }
     }
   }
@@ -664,7 +703,7 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
     for (int i = 0; i < 8; ++i) v[i] = __ldcs(xr + base + 32 * i + lane);
     if (SCALED) Chunk<T, 8, EMU>::scale(cf, E, v);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) __stcs(yr + base + 32 * i + lane, Chunk<T, 8, EMU>::output(i, h, v[i]));
+    for (int i = 0; i < 8; ++i) __stcs(yr + base + 32 * i + lane, Chunk<T, 8, EMU>::template output<OUTK>(i, h, v[i]));
   }
   if (base < n) {
     T v[8];
@@ -678,7 +717,7 @@ __device__ __forceinline__ void stream_write(const T* __restrict__ xr, T* yr, in
     for (int i = 0; i < 8; ++i) {
       if (base + 32 * i >= n) break;  // warp-uniform: no work for chunks past the end
       const int k = base + 32 * i + lane;
-      if (k < n) __stcs(yr + k, Chunk<T, 8, EMU>::output(i, h, v[i]));
+      if (k < n) __stcs(yr + k, Chunk<T, 8, EMU>::template output<OUTK>(i, h, v[i]));
     }
   }
 }
@@ -798,30 +837,30 @@ __device__ __forceinline__ int stream_pass1(const T* __restrict__ xr, T* yr, int
 
 // Pass 2 for a vector with factor code `code` (not CODE_ZERO); EMU selects
 // the binary64 integer-pipe steps.
-template <typename T, bool EMU, bool TAIL_SKIP = true>
+template <typename T, bool EMU, bool TAIL_SKIP = true, bool LANE = false>
 __device__ __forceinline__ T stream_pass2(const T* __restrict__ xr, int n, int lane, int code) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  return code != CODE_ONE ? stream_sum_squares<T, true, EMU, TAIL_SKIP>(xr, n, lane, cf, E)
-                          : stream_sum_squares<T, false, EMU, TAIL_SKIP>(xr, n, lane, cf, E);
+  return code != CODE_ONE ? stream_sum_squares<T, true, EMU, TAIL_SKIP, LANE>(xr, n, lane, cf, E)
+                          : stream_sum_squares<T, false, EMU, TAIL_SKIP, LANE>(xr, n, lane, cf, E);
 }
 
 // Pass 3: x^ = h x~.
-template <typename T, bool EMU>
+template <typename T, bool EMU, int OUTK = F64_EMU_OUTPUTS_OF_8>
 __device__ __forceinline__ void stream_pass3(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code) {
   const T cf = factor_of<T, true>(code);
   const int E = Pow2Scale<T>::exponent(code);
-  if (code != CODE_ONE) stream_write<T, true, EMU>(xr, yr, n, lane, h, cf, E);
-  else stream_write<T, false, EMU>(xr, yr, n, lane, h, cf, E);
+  if (code != CODE_ONE) stream_write<T, true, EMU, OUTK>(xr, yr, n, lane, h, cf, E);
+  else stream_write<T, false, EMU, OUTK>(xr, yr, n, lane, h, cf, E);
 }
 
 // The hardware-operation passes of a binary64 vector that the integer-pipe
 // steps do not take (rare: components 2^511 times smaller than the largest,
 // subnormals with sigma_min, infinities, NaN).  Out of line, so that the
 // common path of the kernels stays small in the instruction cache.
-template <typename T>
+template <typename T, bool LANE = false>
 __device__ __noinline__ T stream_pass2_slow(const T* __restrict__ xr, int n, int lane, int code) {
-  return stream_pass2<T, false>(xr, n, lane, code);
+  return stream_pass2<T, false, true, LANE>(xr, n, lane, code);
 }
 template <typename T>
 __device__ __noinline__ void stream_pass3_slow(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code) {
@@ -834,16 +873,16 @@ __device__ __noinline__ void stream_pass3_slow(const T* __restrict__ xr, T* yr, 
 // TAIL_SKIP: the last, partial round adds only the chunks that hold terms
 // (warp-uniform branches: a gain for short vectors; for the dense binary64
 // rows, which have no partial round, the branches cost 6 % and are left out).
-template <typename T, bool TAIL_SKIP = true>
+template <typename T, bool TAIL_SKIP = true, bool LANE = false>
 __device__ __forceinline__ T stream_pass2_any(const T* __restrict__ xr, int n, int lane, int code, bool emu) {
-  if (sizeof(T) == 4) return stream_pass2<T, false, TAIL_SKIP>(xr, n, lane, code);
-  return emu ? stream_pass2<T, true, TAIL_SKIP>(xr, n, lane, code) : stream_pass2_slow<T>(xr, n, lane, code);
+  if (sizeof(T) == 4) return stream_pass2<T, false, TAIL_SKIP, LANE>(xr, n, lane, code);
+  return emu ? stream_pass2<T, true, TAIL_SKIP, LANE>(xr, n, lane, code) : stream_pass2_slow<T, LANE>(xr, n, lane, code);
 }
-template <typename T>
+template <typename T, int OUTK = F64_EMU_OUTPUTS_OF_8>
 __device__ __forceinline__ void stream_pass3_any(const T* __restrict__ xr, T* yr, int n, int lane, T h, int code,
                                                  bool emu) {
   if (sizeof(T) == 4) stream_pass3<T, false>(xr, yr, n, lane, h, code);
-  else if (emu) stream_pass3<T, true>(xr, yr, n, lane, h, code);
+  else if (emu) stream_pass3<T, true, OUTK>(xr, yr, n, lane, h, code);
   else stream_pass3_slow<T>(xr, yr, n, lane, h, code);
 }
 
@@ -895,12 +934,18 @@ __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T*
 // each pass keeps the kernel small.
 // TAIL_SKIP as in stream_pass2_any: true for ragged vectors (partial last
 // rounds), false for dense rows.
-template <typename T, int NB, int MAX_N, bool TAIL_SKIP = false, typename Item>
+// OUTK: outputs of every 8 formed on the integer pipe (binary64).
+template <typename T, int NB, int MAX_N, bool TAIL_SKIP = false, int OUTK = F64_EMU_OUTPUTS_OF_8, typename Item>
 __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int nb, int lane, const VecOut<T>& out) {
+  // binary64 pairs: the shuffle levels of both trees at once (stream_tree_shfl2;
+  // binary64 forms no speculative sums, so every sum comes from pass 2)
+  constexpr bool PACK = NB == 2 && sizeof(T) == 8;
   T s = T(1);
   int code_l = CODE_ONE;  // lane j < nb: the code of vector j
   unsigned codes = 0;     // 2 bits per vector
   unsigned emu_m = 0;
+  T part0 = T(0), part1 = T(0);  // PACK: lane partials of vectors 0 and 1
+  int len0 = 0, len1 = 0;
 #pragma unroll 1
   for (int j = 0; j < NB; ++j) {
     int code = CODE_ZERO;
@@ -920,15 +965,30 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
         code = stream_pass1<T>(xr, yr, n, lane, out, vec, emu, sj, have_s);
       }
       if (code != CODE_ZERO) {
-        if (!have_s) sj = stream_pass2_any<T, TAIL_SKIP>(xr, n, lane, code, emu);
-        if (lane == j) {
-          s = sj;
-          code_l = code;
+        if (PACK) {
+          const T pj = stream_pass2_any<T, TAIL_SKIP, true>(xr, n, lane, code, emu);
+          if (j == 0) {
+            part0 = pj;
+            len0 = n;
+          } else {
+            part1 = pj;
+            len1 = n;
+          }
+        } else {
+          if (!have_s) sj = stream_pass2_any<T, TAIL_SKIP>(xr, n, lane, code, emu);
+          if (lane == j) s = sj;
         }
+        if (lane == j) code_l = code;
         emu_m |= (emu ? 1u : 0u) << j;
       }
     }
     codes |= (unsigned)code << (2 * j);
+  }
+  if (PACK) {
+    const T r = stream_tree_shfl2<T>(part0, len0, part1, len1, lane);
+    const T t0 = __shfl_sync(FULL, r, 0), t1 = __shfl_sync(FULL, r, 16);
+    if (lane == 0 && (codes & 3u) != (unsigned)CODE_ZERO) s = t0;
+    if (lane == 1 && ((codes >> 2) & 3u) != (unsigned)CODE_ZERO) s = t1;
   }
   const T rt = FP<T>::sqrt(s);
   const T h = FP<T>::rcp(rt);
@@ -943,7 +1003,7 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
       int64_t vec;
       item(j, xr, yr, n, vec);
       const T hj = __shfl_sync(FULL, h, j);
-      if (yr) stream_pass3_any<T>(xr, yr, n, lane, hj, code, (emu_m >> j) & 1u);
+      if (yr) stream_pass3_any<T, OUTK>(xr, yr, n, lane, hj, code, (emu_m >> j) & 1u);
       if (lane == j) out.put(vec, r, h, code);
     }
   }
@@ -970,7 +1030,7 @@ __device__ __forceinline__ void warp_forward_tail(T (&v)[CH][V], T* yr, int n, i
       if (k0 < n) {
         T o[V];
 #pragma unroll
-        for (int e = 0; e < V; ++e) o[e] = Chunk<T, CH * V, EMU>::output(c * V + e, h, v[c][e]);
+        for (int e = 0; e < V; ++e) o[e] = Chunk<T, CH * V, EMU>::template output<>(c * V + e, h, v[c][e]);
         Vec<T, V>::store(yr + k0, o);
       }
     }
