@@ -598,18 +598,60 @@ __device__ __forceinline__ T stream_tree_shfl(T v, int n, int lane) {
 // the remaining levels run inside each half-warp and serve both vectors with
 // one instruction.  The additions and their order are those of CR(n) for each
 // vector.  Returns A's total in lane 0 and B's in lane 16.
+// Stride 16 of stream_tree_shfl2: slot i (i < 16) of A in lane i, of B in
+// lane 16 + i.
+template <typename T>
+__device__ __forceinline__ T stream_tree_shfl2_level16(T a, int na, T b, int nb, int lane) {
+  const bool hi = lane >= 16;
+  const int i = lane & 15;
+  const int used = hi ? (nb < CR_SLOTS ? nb : CR_SLOTS) : (na < CR_SLOTS ? na : CR_SLOTS);
+  const T o16 = __shfl_xor_sync(FULL, hi ? a : b, 16);  // lane i gets A's slot i + 16, lane 16 + i B's slot i
+  // lane 16 + i holds B's slot 16 + i itself: added to slot i when it holds a
+  // term, otherwise slot i alone moves there
+  T r = hi ? b : a;
+  if (i + 16 < used) r = FP<T>::add(r, o16);
+  else if (hi) r = o16;
+  return r;
+}
+
 template <typename T>
 __device__ __forceinline__ T stream_tree_shfl2(T a, int na, T b, int nb, int lane) {
   const bool hi = lane >= 16;
   const int i = lane & 15;
   const int used = hi ? (nb < CR_SLOTS ? nb : CR_SLOTS) : (na < CR_SLOTS ? na : CR_SLOTS);
-  const T o16 = __shfl_xor_sync(FULL, hi ? a : b, 16);  // lane i gets A's slot i + 16, lane 16 + i B's slot i
-  T r = hi ? b : a;
-  if (i + 16 < used) r = FP<T>::add(r, o16);
+  T r = stream_tree_shfl2_level16<T>(a, na, b, nb, lane);
 #pragma unroll
   for (int p = 8; p >= 1; p >>= 1) {
     const T o = __shfl_xor_sync(FULL, r, p);
     if (i < p && i + p < used) r = FP<T>::add(r, o);
+  }
+  return r;
+}
+
+// The same for four vectors A, B, C, D (lane partials a, b, c, d; lengths
+// na .. nd).  Stride 16 as in stream_tree_shfl2, once for (A, B) and once for
+// (C, D); stride 8 then exchanges between the two: in each half-warp, lanes
+// i < 8 add slot i + 8 into slot i of A (or B), lanes i >= 8 slot i into
+// slot i - 8 of C (or D), so that each quarter-warp holds the first 8 slots
+// of one vector (lanes 0-7 A, 8-15 C, 16-23 B, 24-31 D) for strides 4, 2, 1.
+// Returns the totals in lanes 0 (A), 16 (B), 8 (C) and 24 (D).
+template <typename T>
+__device__ __forceinline__ T stream_tree_shfl4(T a, int na, T b, int nb, T c, int nc, T d, int nd, int lane) {
+  const T r1 = stream_tree_shfl2_level16<T>(a, na, b, nb, lane);
+  const T r2 = stream_tree_shfl2_level16<T>(c, nc, d, nd, lane);
+  const bool hi = lane >= 16;
+  const int i = lane & 15;
+  const bool lo8 = i < 8;
+  const int nv = lo8 ? (hi ? nb : na) : (hi ? nd : nc);
+  const int used = nv < CR_SLOTS ? nv : CR_SLOTS;
+  const T o8 = __shfl_xor_sync(FULL, lo8 ? r2 : r1, 8);
+  const int j = i & 7;  // the slot this lane holds after the exchange
+  T r = lo8 ? r1 : r2;
+  if (j + 8 < used) r = FP<T>::add(r, o8);
+#pragma unroll
+  for (int p = 4; p >= 1; p >>= 1) {
+    const T o = __shfl_xor_sync(FULL, r, p);
+    if (j < p && j + p < used) r = FP<T>::add(r, o);
   }
   return r;
 }
@@ -937,15 +979,16 @@ __device__ __forceinline__ void warp_forward_stream(const T* __restrict__ xr, T*
 // OUTK: outputs of every 8 formed on the integer pipe (binary64).
 template <typename T, int NB, int MAX_N, bool TAIL_SKIP = false, int OUTK = F64_EMU_OUTPUTS_OF_8, typename Item>
 __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int nb, int lane, const VecOut<T>& out) {
-  // binary64 pairs: the shuffle levels of both trees at once (stream_tree_shfl2;
-  // binary64 forms no speculative sums, so every sum comes from pass 2)
-  constexpr bool PACK = NB == 2 && sizeof(T) == 8;
+  // binary64 batches of 2 or 4: the shuffle levels of all trees at once
+  // (stream_tree_shfl2 / stream_tree_shfl4; binary64 forms no speculative
+  // sums, so every sum comes from pass 2)
+  constexpr bool PACK = (NB == 2 || NB == 4) && sizeof(T) == 8;
   T s = T(1);
   int code_l = CODE_ONE;  // lane j < nb: the code of vector j
   unsigned codes = 0;     // 2 bits per vector
   unsigned emu_m = 0;
-  T part0 = T(0), part1 = T(0);  // PACK: lane partials of vectors 0 and 1
-  int len0 = 0, len1 = 0;
+  T part0 = T(0), part1 = T(0), part2 = T(0), part3 = T(0);  // PACK: lane partials of the vectors
+  int len0 = 0, len1 = 0, len2 = 0, len3 = 0;
 #pragma unroll 1
   for (int j = 0; j < NB; ++j) {
     int code = CODE_ZERO;
@@ -970,9 +1013,15 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
           if (j == 0) {
             part0 = pj;
             len0 = n;
-          } else {
+          } else if (NB == 2 || j == 1) {  // (pairs: no registers for vectors 2 and 3)
             part1 = pj;
             len1 = n;
+          } else if (j == 2) {
+            part2 = pj;
+            len2 = n;
+          } else {
+            part3 = pj;
+            len3 = n;
           }
         } else {
           if (!have_s) sj = stream_pass2_any<T, TAIL_SKIP>(xr, n, lane, code, emu);
@@ -984,11 +1033,17 @@ __device__ __forceinline__ void warp_forward_stream_batch(const Item& item, int 
     }
     codes |= (unsigned)code << (2 * j);
   }
-  if (PACK) {
+  if (PACK && NB == 2) {
     const T r = stream_tree_shfl2<T>(part0, len0, part1, len1, lane);
     const T t0 = __shfl_sync(FULL, r, 0), t1 = __shfl_sync(FULL, r, 16);
     if (lane == 0 && (codes & 3u) != (unsigned)CODE_ZERO) s = t0;
     if (lane == 1 && ((codes >> 2) & 3u) != (unsigned)CODE_ZERO) s = t1;
+  } else if (PACK) {
+    const T r = stream_tree_shfl4<T>(part0, len0, part1, len1, part2, len2, part3, len3, lane);
+    // totals: vector 0 in lane 0, 1 in lane 16, 2 in lane 8, 3 in lane 24
+    const int src = lane < 4 ? ((lane & 1) << 4) | ((lane & 2) << 2) : 0;
+    const T t = __shfl_sync(FULL, r, src);
+    if (lane < 4 && ((codes >> (2 * lane)) & 3u) != (unsigned)CODE_ZERO) s = t;
   }
   const T rt = FP<T>::sqrt(s);
   const T h = FP<T>::rcp(rt);

@@ -297,7 +297,8 @@ def test_stream_speculation_falls_back(rph, n):
     _forward(rph, "f32", n, "stream", x, f"f32 n={n} speculation")
 
 
-@pytest.mark.parametrize("f,n,cnt", [("f64", 300, 11), ("f64", 1000, 9), ("f64", 40, 13), ("f32", 700, 9)])
+@pytest.mark.parametrize("f,n,cnt", [("f64", 300, 11), ("f64", 1000, 9), ("f64", 40, 13), ("f64", 20, 13),
+                                     ("f64", 9, 11), ("f32", 700, 9)])
 def test_pairs_forward_matches_oracle(rph, f, n, cnt):
     """Two vectors of different lengths per warp sharing one square root and
     reciprocal, with the partial-round skip (the ragged binary64 warp items),
