@@ -169,6 +169,17 @@ ngb_status ngb_plan_set_graphs(ngb_plan* plan, int32_t enable);
  * NGB_VALIDATE_OFFSETS) offsets[0] != 0. */
 ngb_status ngb_query_status(ngb_plan* plan, ngb_stream_t stream);
 
+/* The opt-in bulk-copy path for binary32 quaternions: with the environment
+ * variable NGB_QUAT_BULK set to "1" when the library first normalizes dense
+ * binary32 quaternions, calls on 16-byte aligned device memory stage the
+ * input through shared memory with bulk copies (cp.async.bulk) instead of
+ * registers; same results, measured slower on GB300, so off by default.
+ * Writes the path's state on the current device to *state: bit 0 once its
+ * kernel has run in this process, bit 1 if one of its bounded waits gave up
+ * (never expected; the outputs of the tiles it did not reach are then not
+ * written).  Synchronous (a device-to-host copy). */
+ngb_status ngb_quat_bulk_state(uint32_t* state);
+
 /*
  * normalize_to_rotation_f32 / _f64 -- Section 4: normalize quaternions
  * q = (q1, q2, q3, q4) (scalar part q4) with Algorithm 7 and write the

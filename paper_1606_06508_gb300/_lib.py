@@ -49,6 +49,7 @@ PROTOTYPES = {
     "ngb_plan_autotune": (ST, [P, P, ctypes.c_char_p, P]),
     "ngb_plan_set_graphs": (ST, [P, I32]),
     "ngb_query_status": (ST, [P, P]),
+    "ngb_quat_bulk_state": (ST, [ctypes.POINTER(U32)]),
     "normalize_to_rotation_f32": (ST, [P, P, P, I64, P]),
     "normalize_to_rotation_f64": (ST, [P, P, P, I64, P]),
     "ngb_copy": (ST, [P, P, I64, P]),

@@ -496,6 +496,13 @@ ngb_status ngb_shard_range(const int64_t* offsets, int64_t count, int32_t world,
   return NGB_OK;
 }
 
+ngb_status ngb_quat_bulk_state(uint32_t* state) {
+  g_last_error.clear();
+  if (!state) return fail(NGB_ERR_INVALID_ARG, "state is NULL");
+  const cudaError_t e = ngb::quat_bulk_state(state);
+  return e == cudaSuccess ? NGB_OK : cuda_fail(e, "ngb_quat_bulk_state");
+}
+
 const char* ngb_last_error(void) { return g_last_error.c_str(); }
 
 const char* ngb_version(void) { return "normgb 0.1.0 (sm_103a)"; }

@@ -404,6 +404,12 @@ inline int grid_for(K kernel, int threads, int64_t work_items, int items_per_blo
 template <typename T, int D>
 cudaError_t launch_small_fwd(const T* x, T* y, VecOut<T> out, int64_t count, bool quat_zero, cudaStream_t s) {
   const bool vec16 = aligned16(x) && aligned16(y);
+  if constexpr (sizeof(T) == 4 && D == 4) {  // opt-in: quat_bulk_enabled()
+    if (count > 0 && quat_bulk_enabled()) {
+      const cudaError_t e = launch_quat_bulk(x, y, out, count, quat_zero, s);
+      if (e != cudaErrorNotSupported) return e;
+    }
+  }
   if constexpr (D * sizeof(T) == 16) {
     if (vec16) {
       auto k = k_small_vec16<T, D>;

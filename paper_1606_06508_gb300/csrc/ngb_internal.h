@@ -24,6 +24,17 @@ template <typename T>
 cudaError_t launch_fixed_backward(const T* y, const T* g, const T* h, const int8_t* c, T* grad, int64_t count,
                                   int dim, cudaStream_t s);
 
+// binary32 quaternions through bulk copies into shared memory (ngb_bulk.cuh;
+// fixed_f32.cu).  Returns cudaErrorNotSupported, launching nothing, unless x
+// and y (when given) are 16-byte aligned device memory.  Taken instead of
+// k_small_vec16 only when quat_bulk_enabled(): the environment variable
+// NGB_QUAT_BULK is "1" when the library first asks (it measured slower).
+cudaError_t launch_quat_bulk(const float* x, float* y, const VecOut<float>& out, int64_t count, bool quat_zero,
+                             cudaStream_t s);
+bool quat_bulk_enabled();
+// The bulk path's state word on the current device (see ngb_quat_bulk_state).
+cudaError_t quat_bulk_state(uint32_t* state);
+
 // Ragged batches: bucket lists produced by the classifier, consumed by one
 // persistent kernel.
 struct RaggedMapping {
