@@ -28,6 +28,7 @@
 #pragma once
 #include "ngb_internal.h"
 #include "ngb_grouppath.cuh"
+#include "ngb_threadpath.cuh"
 
 namespace ngb {
 
@@ -149,30 +150,6 @@ __device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr,
     code = normalize_thread_generic<T, 16>(xr, yr, n, r, h);
   }
   out.put(vec, r, h, code);
-}
-
-template <typename T>
-__device__ __forceinline__ void thread_item_bwd(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr, int n,
-                                                T h, int code) {
-  if (n <= 4) {
-    T yv[4], gv[4], o[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      yv[k] = k < n ? yr[k] : T(0);
-      gv[k] = k < n ? gr[k] : T(0);
-    }
-    switch (n) {
-      case 1: backward_small<T, 1>(yv, gv, h, code, o); break;
-      case 2: backward_small<T, 2>(yv, gv, h, code, o); break;
-      case 3: backward_small<T, 3>(yv, gv, h, code, o); break;
-      default: backward_small<T, 4>(yv, gv, h, code, o); break;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-      if (k < n) gradr[k] = o[k];
-  } else {
-    backward_thread_generic<T, 16>(yr, gr, n, h, code, gradr);
-  }
 }
 
 template <typename T>

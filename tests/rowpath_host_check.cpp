@@ -24,7 +24,9 @@
 //           that the groups of a warp differ in length
 // Backward paths read y, g (count x n each), h (count) and code (count bytes)
 // and write grad (count x n): warp_bwd (n <= 1024), stream_bwd, block_bwd,
-// group8_bwd, group16_bwd (lengths as the group forward paths).
+// group8_bwd, group16_bwd (lengths as the group forward paths), thread_bwd
+// (n <= 16, one thread per row, the ragged thread items; row i holds a
+// vector of length 1 + i mod n).
 // Path ghr: see run_ghr.
 #include <cstdio>
 #include <cstdlib>
@@ -33,6 +35,7 @@
 #include <vector>
 
 #include "ngb_grouppath.cuh"
+#include "ngb_threadpath.cuh"
 
 using namespace ngb;
 
@@ -175,6 +178,12 @@ static void run_path(Rows<T>& d, const std::string& path) {
       const int lane = threadIdx.x & 31;
       for (int64_t row = threadIdx.x >> 5; row < d.count; row += 2)
         warp_forward_stream<T>(d.x.data() + row * n, d.y.data() + row * n, n, lane, out, row);
+    });
+  } else if (path == "thread_bwd") {  // one thread per row, row i of length 1 + i mod n (n <= 16)
+    hemu::run_block(32, [&] {
+      for (int64_t row = threadIdx.x; row < d.count; row += 32)
+        thread_item_bwd<T>(d.y.data() + row * n, d.g.data() + row * n, d.grad.data() + row * n,
+                           1 + (int)(row % n), d.h[row], d.code[row]);
     });
   } else if (path == "stream_bwd") {
     hemu::run_block(64, [&] {
@@ -329,6 +338,7 @@ int main(int argc, char** argv) {
   }
   if (!strcmp(argv[3], "ghr")) return run_ghr(atoi(argv[2]), argv[4], argv[5]);
   const int n = atoi(argv[2]);
-  if (n < 5 || n > MAX_LEN) { fprintf(stderr, "n must be in 5..2^20\n"); return 2; }
+  const bool short_ok = !strcmp(argv[3], "thread_bwd");
+  if (n < (short_ok ? 1 : 5) || n > (short_ok ? 16 : MAX_LEN)) { fprintf(stderr, "n out of range for the path\n"); return 2; }
   return !strcmp(argv[1], "f32") ? run<float>(n, argv[3], argv[4], argv[5]) : run<double>(n, argv[3], argv[4], argv[5]);
 }

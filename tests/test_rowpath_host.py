@@ -281,6 +281,39 @@ def test_group_backward_product_by_h_over_the_exponent_range(rph, n, w):
     assert_bits(_pack(rawb.view(np.float64).reshape(cnt, n), lengths), og, f"f64 group{w} product by h")
 
 
+@pytest.mark.parametrize("f,n", [("f64", 16), ("f64", 7), ("f32", 16)])
+def test_thread_backward_over_the_exponent_range(rph, f, n):
+    """Thread items of the ragged backward (one thread per vector, lengths 1
+    .. n), binary64 with the integer-pipe products: inputs and upstream
+    gradients over the whole exponent range, zero vectors and NaN, so that
+    the products fall inside and outside f64emu's ranges vector by vector;
+    every gradient against the oracle."""
+    dt = DT[f]
+    rng = np.random.default_rng(17 * n + len(f))
+    cnt = 96
+    lengths = 1 + np.arange(cnt) % n
+    sx = np.array([-1000, -600, -200, 0, 200, 600, 1000]) if f == "f64" else np.array([-120, -60, 0, 60, 120])
+    sg = (np.array([-1074, -1060, -1022, -1000, -900, -600, -300, 0, 300, 600, 900, 1000, 1015]) if f == "f64"
+          else np.array([-149, -140, -126, -100, -50, 0, 50, 100, 120]))
+    x = (rng.standard_normal((cnt, n)) * 2.0 ** sx[np.arange(cnt) % sx.size][:, None]).astype(dt)
+    x[5] = 0
+    x[11, 0] = np.nan
+    for i, m in enumerate(lengths):
+        x[i, m:] = 0
+    off = synth.offsets_from_lengths(lengths)
+    oy, _, oh, oc = oracle.normalize(_pack(x, lengths), dim=0, offsets=off)
+    g = (rng.standard_normal((cnt, n)) * 2.0 ** sg[(np.arange(cnt) * 5) % sg.size][:, None]).astype(dt)
+    g[::3, 0] = dt(2.0 ** (1000 if f == "f64" else 120))
+    g[1::3, -1] = np.finfo(dt).smallest_subnormal
+    yr = np.zeros((cnt, n), dt)
+    for i, m in enumerate(lengths):
+        yr[i, :m] = oy[off[i]:off[i + 1]]
+        g[i, m:] = 0
+    og = oracle.backward(oy, _pack(g, lengths), oh, oc, dim=0, offsets=off)
+    rawb = _call(rph, f, n, "thread_bwd", [yr, g, oh, oc.astype(np.int8)])
+    assert_bits(_pack(rawb.view(dt).reshape(cnt, n), lengths), og, f"{f} thread backward n<={n}")
+
+
 @pytest.mark.parametrize("n", [1025, 5000])
 def test_stream_speculation_falls_back(rph, n):
     """binary32 streaming rows whose first 256 components select another
