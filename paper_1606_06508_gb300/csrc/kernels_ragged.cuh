@@ -115,43 +115,6 @@ __global__ void __launch_bounds__(CLASSIFY_THREADS)
   }
 }
 
-// One vector of n <= 16 components by one thread (vector zero rule for n = 4).
-template <typename T>
-__device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr, int n, const VecOut<T>& out,
-                                                int64_t vec) {
-  T r, h;
-  int code;
-  if (n <= 4) {
-    T xv[4], yv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) xv[k] = k < n ? xr[k] : T(0);
-    bool done = false;
-    if constexpr (sizeof(T) == 8 && SMALL_F64_INTEGER) {  // one integer-pipe form for every n <= 4
-      const SmallKeysF64<4> kk(xv);
-      if (kk.ok) {
-        code = normalize_small_f64_int<4>(xv, yv, r, h, false, kk);
-        done = true;
-      }
-    }
-    if (!done) {
-      switch (n) {
-        case 1: code = normalize_small_hw<T, 1>(xv, yv, r, h, false); break;
-        case 2: code = normalize_small_hw<T, 2>(xv, yv, r, h, false); break;
-        case 3: code = normalize_small_hw<T, 3>(xv, yv, r, h, false); break;
-        default: code = normalize_small_hw<T, 4>(xv, yv, r, h, false); break;
-      }
-    }
-    if (yr) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < n) yr[k] = yv[k];
-    }
-  } else {
-    code = normalize_thread_generic<T, 16>(xr, yr, n, r, h);
-  }
-  out.put(vec, r, h, code);
-}
-
 template <typename T>
 struct RaggedArgs {
   const T* x;          // forward input, or y for the backward pass

@@ -1,6 +1,7 @@
-// ngb_threadpath.cuh -- the backward of a short vector (n <= 16) by one
-// thread: the ragged thread items.  dot = y . g (left to right for n <= 4,
-// the order CR(n) otherwise), grad_k = ((g_k - y_k dot) h) c.
+// ngb_threadpath.cuh -- a short vector (n <= 16) by one thread: the ragged
+// thread items, forward (Algorithms 5-7 for n <= 4, the generic steps in the
+// order CR(n) otherwise) and backward (dot = y . g, left to right for n <= 4,
+// the order CR(n) otherwise; grad_k = ((g_k - y_k dot) h) c).
 #pragma once
 #include "ngb_rowpath.cuh"
 
@@ -10,6 +11,44 @@ namespace ngb {
 // (thread_item_bwd_f64).  Ragged binary64 forward + backward per step:
 // 1.513-1.523 ms against 1.536-1.538 ms with the hardware products.
 constexpr bool THREAD_BWD_F64_INT = true;
+
+// One vector of n <= 16 components by one thread (vector zero rule for n = 4).
+template <typename T>
+__device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr, int n, const VecOut<T>& out,
+                                                int64_t vec) {
+  T r, h;
+  int code;
+  if (n <= 4) {
+    T xv[4], yv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = k < n ? xr[k] : T(0);
+    bool done = false;
+    if constexpr (sizeof(T) == 8 && SMALL_F64_INTEGER) {  // one integer-pipe form for every n <= 4
+      const SmallKeysF64<4> kk(xv);
+      if (kk.ok) {
+        code = normalize_small_f64_int<4>(xv, yv, r, h, false, kk);
+        done = true;
+      }
+    }
+    if (!done) {
+      switch (n) {
+        case 1: code = normalize_small_hw<T, 1>(xv, yv, r, h, false); break;
+        case 2: code = normalize_small_hw<T, 2>(xv, yv, r, h, false); break;
+        case 3: code = normalize_small_hw<T, 3>(xv, yv, r, h, false); break;
+        default: code = normalize_small_hw<T, 4>(xv, yv, r, h, false); break;
+      }
+    }
+    if (yr) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < n) yr[k] = yv[k];
+    }
+  } else {
+    code = normalize_thread_generic<T, 16>(xr, yr, n, r, h);
+  }
+  out.put(vec, r, h, code);
+}
+
 
 // With the hardware operations.
 template <typename T>

@@ -18,6 +18,8 @@
 //           root and reciprocal and the partial-round skip (the ragged
 //           binary64 warp items: warp_forward_stream_batch<T, 2, MAX_LEN, true>);
 //           row i holds a vector of length n - (i mod 5) (at least 5)
+//   thread  one thread per row (the ragged thread items, thread_item_fwd),
+//           n <= 16; row i holds a vector of length 1 + i mod n
 //   group8, group16  groups of W = 8 or 16 lanes, 32 / W rows per warp
 //           (csrc/ngb_grouppath.cuh), n <= 8 W; row i holds a vector of
 //           length n - (i mod 5) (at least 5) in its first components, so
@@ -179,6 +181,11 @@ static void run_path(Rows<T>& d, const std::string& path) {
       for (int64_t row = threadIdx.x >> 5; row < d.count; row += 2)
         warp_forward_stream<T>(d.x.data() + row * n, d.y.data() + row * n, n, lane, out, row);
     });
+  } else if (path == "thread") {  // one thread per row, row i of length 1 + i mod n (n <= 16)
+    hemu::run_block(32, [&] {
+      for (int64_t row = threadIdx.x; row < d.count; row += 32)
+        thread_item_fwd<T>(d.x.data() + row * n, d.y.data() + row * n, 1 + (int)(row % n), out, row);
+    });
   } else if (path == "thread_bwd") {  // one thread per row, row i of length 1 + i mod n (n <= 16)
     hemu::run_block(32, [&] {
       for (int64_t row = threadIdx.x; row < d.count; row += 32)
@@ -338,7 +345,7 @@ int main(int argc, char** argv) {
   }
   if (!strcmp(argv[3], "ghr")) return run_ghr(atoi(argv[2]), argv[4], argv[5]);
   const int n = atoi(argv[2]);
-  const bool short_ok = !strcmp(argv[3], "thread_bwd");
+  const bool short_ok = !strcmp(argv[3], "thread_bwd") || !strcmp(argv[3], "thread");
   if (n < (short_ok ? 1 : 5) || n > (short_ok ? 16 : MAX_LEN)) { fprintf(stderr, "n out of range for the path\n"); return 2; }
   return !strcmp(argv[1], "f32") ? run<float>(n, argv[3], argv[4], argv[5]) : run<double>(n, argv[3], argv[4], argv[5]);
 }

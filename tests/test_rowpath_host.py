@@ -281,6 +281,37 @@ def test_group_backward_product_by_h_over_the_exponent_range(rph, n, w):
     assert_bits(_pack(rawb.view(np.float64).reshape(cnt, n), lengths), og, f"f64 group{w} product by h")
 
 
+@pytest.mark.parametrize("f,n", [("f64", 16), ("f64", 9), ("f32", 16)])
+def test_thread_forward_matches_oracle(rph, f, n):
+    """Thread items of the ragged forward (one thread per vector, lengths
+    1 .. n): binary64 with the integer-pipe scale, squares and outputs, on
+    vectors over the whole exponent range, at the limits of the integer-pipe
+    steps (f64_range_edges), zero vectors, NaN and infinities."""
+    dt = DT[f]
+    cnt = 120
+    lengths = 1 + np.arange(cnt) % n
+    if f == "f64":
+        x = np.concatenate([f64_range_edges(cnt // 2, n, seed=n), _rows(f, cnt - cnt // 2, n, seed=3 * n)])
+    else:
+        x = _rows(f, cnt, n, seed=3 * n)
+    x[7] = 0
+    x[13, 0] = np.inf
+    x[19, -1] = np.nan
+    x = x.astype(dt)
+    for i, m in enumerate(lengths):
+        x[i, m:] = 0
+    off = synth.offsets_from_lengths(lengths)
+    oy, orr, oh, oc = oracle.normalize(_pack(x, lengths), dim=0, offsets=off)
+    raw = _call(rph, f, n, "thread", [x.reshape(-1)])
+    s_ = dt(0).itemsize
+    y = raw[: cnt * n * s_].view(dt).reshape(cnt, n)
+    what = f"{f} thread forward n<={n}"
+    assert_bits(_pack(y, lengths), oy, what + " y")
+    assert_bits(raw[cnt * n * s_: (cnt * n + cnt) * s_].view(dt), orr, what + " norm")
+    assert_bits(raw[(cnt * n + cnt) * s_: (cnt * n + 2 * cnt) * s_].view(dt), oh, what + " h")
+    assert_bits(raw[(cnt * n + 2 * cnt) * s_:].view(np.int8), oc, what + " code")
+
+
 @pytest.mark.parametrize("f,n", [("f64", 16), ("f64", 7), ("f32", 16)])
 def test_thread_backward_over_the_exponent_range(rph, f, n):
     """Thread items of the ragged backward (one thread per vector, lengths 1
