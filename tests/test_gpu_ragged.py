@@ -92,6 +92,40 @@ def test_ragged_backward_all_mappings(dev, f):
         assert_bits(_np(gr), og, f"{f} backward mapping={m}")
 
 
+def test_ragged_f64_backward_over_the_exponent_range(dev):
+    """binary64 ragged backward with inputs and upstream gradients over the
+    whole exponent range, on thread, group and warp items: the products on
+    the integer pipes are taken vector by vector (the range tests of the
+    warp, group and thread backward), so vectors on both sides of every test
+    meet in one batch; every gradient against the oracle, under the default
+    mapping and one with thread_max 4."""
+    from paper_1606_06508_gb300 import api
+    rng = np.random.default_rng(23)
+    count = 6007
+    lengths = synth.ragged_lengths(count, seed=23, kind="loguniform", nmax=1024)
+    off = synth.offsets_from_lengths(lengths)
+    sx = rng.integers(-1000, 1001, size=count)
+    x = rng.standard_normal(int(off[-1])) * np.ldexp(1.0, np.repeat(sx, lengths))
+    sg = rng.choice(np.array([-1074, -1060, -1022, -1000, -900, -600, -300, 0, 300, 600, 900, 1000, 1015]), count)
+    g = rng.standard_normal(int(off[-1])) * np.ldexp(1.0, np.repeat(sg, lengths))
+    heads = off[:-1][lengths > 0]
+    g[heads[::7]] = 2.0 ** 1000
+    g[heads[1::7]] = 5e-324
+    x[off[5]:off[6]] = 0
+    oy, orr, oh, oc = oracle.normalize(x, dim=0, offsets=off)
+    og = oracle.backward(oy, g, oh, oc, dim=0, offsets=off)
+    xt, offt, gt = _to(dev, x), _to(dev, off), _to(dev, g)
+    plan = api.Plan(count, xt.dtype)
+    for m in (None, (4, 8192, 256, 0)):
+        if m:
+            plan.set_mapping(*m)
+        y, h, c = api.normalize(xt, offt, save=True, plan=plan)
+        assert_bits(_np(y), oy, f"f64 exponent range forward mapping={m}")
+        gr = api.normalize_backward(y, gt, h, c, offt, plan=plan)
+        assert_bits(_np(gr), og, f"f64 exponent range backward mapping={m}")
+    assert plan.query_status() == 0
+
+
 def test_graph_replay_with_new_buffers(dev):
     """Calls with other x / y buffers on the same plan re-record the graph."""
     from paper_1606_06508_gb300 import api
