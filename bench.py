@@ -70,9 +70,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def quat_bulk_requested() -> bool:
+    """The library's opt-in bulk-copy path for binary32 quaternions (read by
+    the library once, at its first dense binary32 quaternion call)."""
+    return os.environ.get("NGB_QUAT_BULK") == "1"
+
+
 def traffic_for(workload: str):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+    summary, if it was taken on the current kernel sources (else None).  The
+    summary is of the default kernels: none under the opt-in bulk path."""
+    if workload == "quat" and quat_bulk_requested():
+        return None, None
     try:
         with open(TRAFFIC_FILE) as f:
             d = json.load(f)
@@ -459,7 +468,8 @@ def build_work(name, count, rank, torch, L, api, synth, mapping=None, part=None)
         return Work(desc=("2^26 binary32 quaternions (float4 AoS), forward: Algorithm 7, 50/50 "
                           "wide-exponent/N(0,1) components") if count == QUAT_COUNT
                     else f"{count} binary32 quaternions, forward (profiling size)",
-                    units=nq, global_units=count, bytes=32 * nq, dtype="f32", kernel="k_small_vec16<float,4>",
+                    units=nq, global_units=count, bytes=32 * nq, dtype="f32",
+                    kernel="k_quat_bulk (NGB_QUAT_BULK=1)" if quat_bulk_requested() else "k_small_vec16<float,4>",
                     launches=1,
                     arrays={"x": x, "y": y}, inputs=["x"], results=["y"], launch=launch,
                     parity=lambda: parity_full(x, y, 4), accuracy=lambda: accuracy_report(x, y, 4),
