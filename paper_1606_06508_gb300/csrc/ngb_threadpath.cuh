@@ -49,8 +49,8 @@ __device__ __forceinline__ void thread_item_fwd(const T* __restrict__ xr, T* yr,
   out.put(vec, r, h, code);
 }
 
-
-// With the hardware operations.
+// Backward of one thread item with the hardware operations (every product
+// and sum on the FP64 pipe).
 template <typename T>
 __device__ __forceinline__ void thread_item_bwd_hw(const T* __restrict__ yr, const T* __restrict__ gr, T* gradr,
                                                    int n, T h, int code) {
@@ -87,7 +87,7 @@ __device__ __noinline__ void thread_item_bwd_hw_call(const T* __restrict__ yr, c
 // grad_h_in_range, as in the warp and group backward); the sums stay on the
 // FP64 pipe.  Any other vector takes the hardware form, out of line.  The
 // thread backward kernel leaves the ALU almost idle and the FP64 pipe busy,
-// so the products move there whole.  Same bits in every case.
+// so all three products move to the integer pipes.  Same bits in every case.
 __device__ __forceinline__ void thread_item_bwd_f64(const double* __restrict__ yr, const double* __restrict__ gr,
                                                     double* gradr, int n, double h, int code) {
   constexpr int NMAX = 16;
